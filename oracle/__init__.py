@@ -1,0 +1,186 @@
+"""FP64 CPU oracle for the FFT power-spectrum path (nbodykit, arXiv:1712.05834).
+
+TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py`` (its ``cpu_baseline`` leg and ``--impl reference`` arm) may import
+this package.  It shares no code with the CUDA library and never imports it.
+
+The arithmetic lives in ``pk_oracle.c`` (plain FP64 loops, one function per
+step of the method).  This module only marshals arrays, calls numpy's FFT as
+the library primitive between painting and binning (Sec. 3.3.1: the real and
+complex fields are related by an r2c FFT), and finalizes the bin sums:
+
+    P(k, mu) = sum h P / sum h - P_shot                      (Sec. 3.4.1)
+    P_l(k)   = (2l + 1) sum h P L_l(mu) / sum h - [l = 0] P_shot
+    P_shot   = L^3 sum(w^2) / sum(w)^2        (= 1 / nbar for unit weights)
+
+Every pin that ties this oracle to the paper and to mathematics is in
+``tests/test_oracle_*.py`` (run with ``-m "not gpu"``).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pk_oracle.c")
+_LIB = os.path.join(_HERE, "_pk_oracle.so")
+_lib = None
+
+WINDOW_ORDER = {"cic": 2, "tsc": 3, "pcs": 4}
+
+
+def build(force: bool = False) -> str:
+    """Compile pk_oracle.c into oracle/_pk_oracle.so with gcc (FP64, no FMA
+    contraction so the k-bin expression rounds exactly as written)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call([
+            "gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+            "-fno-fast-math", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        d, i, i64, p = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+        lib.oracle_window_weight.argtypes = [i, d]
+        lib.oracle_window_weight.restype = d
+        lib.oracle_paint.argtypes = [p, p, i64, d, i, i, d, p]
+        lib.oracle_paint.restype = i
+        lib.oracle_kbin.argtypes = [i64, d, d, d]
+        lib.oracle_kbin.restype = i64
+        lib.oracle_mubin.argtypes = [i64, i64, i64]
+        lib.oracle_mubin.restype = i64
+        lib.oracle_bin.argtypes = [p, p, i, d, i, i, d, d, d, i, i] + [p] * 9
+        lib.oracle_bin.restype = i
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else ctypes.c_void_p(0)
+
+
+def _order(window) -> int:
+    return WINDOW_ORDER[window] if isinstance(window, str) else int(window)
+
+
+def window_weight(window, d: float) -> float:
+    """B-spline window of order p at distance d cells (Sec. 3.3.2)."""
+    return _load().oracle_window_weight(_order(window), float(d))
+
+
+def kbin(m: int, box_size: float, kmin: float, dk: float) -> int:
+    return _load().oracle_kbin(int(m), float(box_size), float(kmin), float(dk))
+
+
+def mubin(m: int, l: int, nmu: int) -> int:
+    return _load().oracle_mubin(int(m), int(l), int(nmu))
+
+
+def paint(pos, weights, box_size: float, nmesh: int, window, shift: float = 0.0):
+    """Painted field F on an (N, N, N) FP64 mesh (Sec. 3.3.1), nodes at c*H."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    mesh = np.zeros((nmesh, nmesh, nmesh), dtype=np.float64)
+    rc = _load().oracle_paint(_ptr(pos), _ptr(w), pos.shape[0], float(box_size),
+                              int(nmesh), _order(window), float(shift), _ptr(mesh))
+    if rc != 0:
+        raise ValueError("oracle_paint: bad arguments")
+    return mesh
+
+
+def r2c(mesh):
+    """Forward r2c transform, F~(n) = sum_c F[c] exp(-2 pi i c.n / N), last axis halved."""
+    return np.fft.rfftn(mesh)
+
+
+def nbins(box_size: float, nmesh: int, dk: float, kmin: float = 0.0, kmax=None) -> int:
+    """nk = floor((kmax - kmin) / dk); kmax defaults to k_N = (pi N) / L."""
+    if kmax is None or kmax <= 0:
+        kmax = (math.pi * nmesh) / box_size
+    return int(math.floor((kmax - kmin) / dk))
+
+
+def bin_modes(F1, F2, box_size, window, compensated, wsum, dk, kmin=0.0, kmax=None, nmu=0):
+    """Raw FFTPower bin sums from stored half-grid transforms (Sec. 3.4.1)."""
+    F1 = np.ascontiguousarray(F1, dtype=np.complex128)
+    N = F1.shape[0]
+    assert F1.shape == (N, N, N // 2 + 1)
+    if F2 is not None:
+        F2 = np.ascontiguousarray(F2, dtype=np.complex128)
+        assert F2.shape == F1.shape
+    nk = nbins(box_size, N, dk, kmin, kmax)
+    nm = max(int(nmu), 0)
+    out = {
+        "modes1d": np.zeros(nk, np.int64), "ksum1d": np.zeros(nk), "psum1d": np.zeros(nk),
+        "p2sum1d": np.zeros(nk), "p4sum1d": np.zeros(nk),
+        "modes2d": np.zeros(nk * max(nm, 1), np.int64), "ksum2d": np.zeros(nk * max(nm, 1)),
+        "musum2d": np.zeros(nk * max(nm, 1)), "psum2d": np.zeros(nk * max(nm, 1)),
+    }
+    rc = _load().oracle_bin(
+        _ptr(F1), _ptr(F2), int(N), float(box_size), _order(window), int(bool(compensated)),
+        float(wsum), float(kmin), float(dk), int(nk), int(nm),
+        _ptr(out["modes1d"]), _ptr(out["ksum1d"]), _ptr(out["psum1d"]), _ptr(out["p2sum1d"]),
+        _ptr(out["p4sum1d"]), _ptr(out["modes2d"]), _ptr(out["ksum2d"]), _ptr(out["musum2d"]),
+        _ptr(out["psum2d"]))
+    if rc != 0:
+        raise ValueError("oracle_bin: bad arguments")
+    out["nk"], out["nmu"] = nk, nm
+    return out
+
+
+def finalize(sums, shot_noise: float, subtract_shot: bool = True):
+    """Bin averages, multipoles and shot-noise subtraction (Sec. 3.4.1)."""
+    nk, nm = sums["nk"], sums["nmu"]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        m1 = sums["modes1d"].astype(np.float64)
+        ps = shot_noise if subtract_shot else 0.0
+        res = {
+            "k": sums["ksum1d"] / m1,
+            "modes": sums["modes1d"].copy(),
+            "power_raw": sums["psum1d"] / m1,
+            "power": sums["psum1d"] / m1 - ps,
+            "poles": np.stack([sums["psum1d"] / m1 - ps,
+                               5.0 * sums["p2sum1d"] / m1,
+                               9.0 * sums["p4sum1d"] / m1]),
+            "shot_noise": shot_noise,
+        }
+        if nm > 0:
+            m2 = sums["modes2d"].astype(np.float64)
+            res["modes2d"] = sums["modes2d"].reshape(nk, nm).copy()
+            res["k2d"] = (sums["ksum2d"] / m2).reshape(nk, nm)
+            res["mu2d"] = (sums["musum2d"] / m2).reshape(nk, nm)
+            res["power2d_raw"] = (sums["psum2d"] / m2).reshape(nk, nm)
+            res["power2d"] = res["power2d_raw"] - ps
+    return res
+
+
+def fft_power(pos, weights, box_size, nmesh, window="cic", interlaced=False,
+              compensated=True, dk=None, kmin=0.0, kmax=None, nmu=0,
+              subtract_shot=True):
+    """The whole path on the CPU in FP64: paint (one or two meshes), r2c FFT,
+    compensate + interlace, bin, multipoles, shot noise."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    if weights is None:
+        wsum = float(pos.shape[0])
+        w2sum = wsum
+    else:
+        w = np.asarray(weights, dtype=np.float64)
+        wsum = float(np.sum(w))
+        w2sum = float(np.sum(w * w))
+    F1 = r2c(paint(pos, weights, box_size, nmesh, window, 0.0))
+    F2 = r2c(paint(pos, weights, box_size, nmesh, window, 0.5)) if interlaced else None
+    sums = bin_modes(F1, F2, box_size, window, compensated, wsum, dk, kmin, kmax, nmu)
+    shot = box_size ** 3 * w2sum / wsum ** 2
+    res = finalize(sums, shot, subtract_shot)
+    res["wsum"], res["w2sum"] = wsum, w2sum
+    res["nk"], res["nmu"] = sums["nk"], sums["nmu"]
+    return res

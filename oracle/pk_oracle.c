@@ -1,0 +1,219 @@
+/*
+ * pk_oracle.c -- plain FP64 CPU oracle for the FFT power-spectrum path of
+ * nbodykit (Hand, Feng et al., arXiv:1712.05834).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the correctness reference that the
+ * CUDA path is compared against.  Only tests/, __graft_entry__.smoke() and
+ * bench.py's cpu_baseline / reference leg may load it.  It shares no code,
+ * header, table or constant with the CUDA library, and the CUDA library never
+ * loads it.
+ *
+ * Everything is FP64 and written as the plainest loop that states the
+ * definition:
+ *
+ *   oracle_window_weight  B-spline mass-assignment windows of order p = 2, 3, 4
+ *                         (CIC, TSC, PCS), Sec. 3.3.2 "From Catalog to Mesh",
+ *                         windows cited there to Hockney & Eastwood.
+ *   oracle_paint          the painted field F(x) = [1 + delta'(x)] V(x) with
+ *                         V = 1 and per-object weights, Sec. 3.3.1 (painting
+ *                         equation); one mesh per call, optionally displaced by
+ *                         a fraction of a cell (the interlaced second mesh,
+ *                         Sec. 3.3.2, "separated by half of a cell size").
+ *   oracle_bin            the FFTPower mode loop, Sec. 3.4.1: window
+ *                         compensation by prod_i sinc^p(pi k_i / 2 k_N)
+ *                         (Eq. window-deconvolution), the interlacing combine,
+ *                         |delta(k)|^2 averaged in k bins, (k, mu) bins and
+ *                         Legendre multipoles l = 0, 2, 4.
+ *
+ * The FFT between paint and bin is a library primitive (numpy's pocketfft),
+ * called from the Python glue in oracle/__init__.py.
+ *
+ * Conventions the paper leaves open (each one also used by the CUDA path and
+ * listed with its reasoning in the design notes):
+ *   - mesh node c sits at position c * H, H = L / N; s = x N / L in cell units;
+ *   - positions are wrapped periodically into [0, L);
+ *   - the interlaced mesh is painted at x + H/2 on every axis and its
+ *     transform is multiplied by exp(+i (kx + ky + kz) H / 2) before averaging;
+ *   - k index of axes x, y follows numpy fftfreq (i' = i for i < N/2, else
+ *     i - N); the r2c axis z stores l = 0 .. N/2 (l = N/2 taken as +N/2);
+ *   - the stored half grid is walked with weight h = 1 on the l = 0 and
+ *     l = N/2 planes and h = 2 elsewhere; the DC mode is never binned;
+ *   - k bin b = floor((kF * sqrt(m) - kmin) / dk) in IEEE FP64, in exactly
+ *     that order, kF = (2 pi) / L, m = i'^2 + j'^2 + l^2; kept iff 0 <= b < nk;
+ *   - mu = l / sqrt(m) in [0, 1]; mu bin q = largest integer with
+ *     q^2 m <= nmu^2 l^2, clamped to nmu - 1 (edges linspace(0,1,nmu+1),
+ *     lower edge inclusive), evaluated in exact integer arithmetic;
+ *   - P(mode) = L^3 |delta(k)|^2 with delta(k) = F~(k) / sum(w).
+ *
+ * Build with -ffp-contract=off: the k-bin expression must round exactly as
+ * written.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* B-spline mass-assignment window of order p evaluated at distance d (cells)
+ * from a mesh node.  Sec. 3.3.2: CIC, TSC, PCS with p = 2, 3, 4. */
+double oracle_window_weight(int p, double d)
+{
+    d = fabs(d);
+    if (p == 2) {
+        return d < 1.0 ? 1.0 - d : 0.0;
+    }
+    if (p == 3) {
+        if (d < 0.5) return 0.75 - d * d;
+        if (d < 1.5) return 0.5 * (1.5 - d) * (1.5 - d);
+        return 0.0;
+    }
+    if (p == 4) {
+        if (d < 1.0) return (4.0 - 6.0 * d * d + 3.0 * d * d * d) / 6.0;
+        if (d < 2.0) return (2.0 - d) * (2.0 - d) * (2.0 - d) / 6.0;
+        return 0.0;
+    }
+    return NAN;
+}
+
+static int64_t mod_n(int64_t c, int64_t n)
+{
+    int64_t r = c % n;
+    return r < 0 ? r + n : r;
+}
+
+/* Paint n objects onto mesh[N][N][N] (C order, z fastest), adding
+ *   F[c] += w_q * prod_a W_p(s_a - c_a)
+ * for every node c within the window support, with s = wrap(x) N / L + shift.
+ * pos is n x 3 FP64, w is n FP64 or NULL (unit weights).  The mesh is not
+ * cleared.  Returns 0, or -1 on bad arguments. */
+int oracle_paint(const double *pos, const double *w, int64_t n, double L, int N,
+                 int p, double shift, double *mesh)
+{
+    if (N < 1 || L <= 0.0 || (p < 2 || p > 4)) return -1;
+    const int64_t NN = (int64_t)N;
+    for (int64_t q = 0; q < n; ++q) {
+        double wa[3][8];
+        int64_t ia[3][8];
+        for (int a = 0; a < 3; ++a) {
+            double x = pos[3 * q + a];
+            x = x - L * floor(x / L);              /* periodic wrap into [0, L) */
+            double s = x * (double)N / L + shift;  /* cell units */
+            int64_t c0 = (int64_t)floor(s - 0.5 * p);
+            for (int k = 0; k < p + 2; ++k) {      /* every node within p/2 */
+                int64_t c = c0 + k;
+                wa[a][k] = oracle_window_weight(p, s - (double)c);
+                ia[a][k] = mod_n(c, NN);
+            }
+        }
+        double wq = w ? w[q] : 1.0;
+        for (int kx = 0; kx < p + 2; ++kx)
+            for (int ky = 0; ky < p + 2; ++ky)
+                for (int kz = 0; kz < p + 2; ++kz) {
+                    double v = wq * wa[0][kx] * wa[1][ky] * wa[2][kz];
+                    if (v == 0.0) continue;
+                    mesh[(ia[0][kx] * NN + ia[1][ky]) * NN + ia[2][kz]] += v;
+                }
+    }
+    return 0;
+}
+
+static double sinc(double x)
+{
+    return x == 0.0 ? 1.0 : sin(x) / x;
+}
+
+/* k bin of integer squared index m: floor((kF sqrt(m) - kmin) / dk), FP64,
+ * evaluated in exactly this order. */
+int64_t oracle_kbin(int64_t m, double L, double kmin, double dk)
+{
+    double kF = (2.0 * M_PI) / L;
+    return (int64_t)floor((kF * sqrt((double)m) - kmin) / dk);
+}
+
+/* mu bin of a mode: largest q with q^2 m <= nmu^2 l^2, clamped to nmu - 1. */
+int64_t oracle_mubin(int64_t m, int64_t l, int64_t nmu)
+{
+    int64_t q = 0;
+    while (q + 1 <= nmu && (q + 1) * (q + 1) * m <= nmu * nmu * l * l) ++q;
+    return q < nmu - 1 ? q : nmu - 1;
+}
+
+/* FFTPower mode loop over the stored half grid of one (or two, interlaced)
+ * r2c transforms F1, F2 of shape [N][N][N/2+1] complex (interleaved re, im).
+ *
+ * For every stored mode except DC:
+ *   delta = F1                                   (not interlaced), or
+ *   delta = (F1 + F2 exp(+i pi (i' + j' + l) / N)) / 2   (interlaced),
+ *   delta /= prod_a sinc(pi n_a / N)^p           (if compensated),
+ *   delta /= wsum;  P = L^3 |delta|^2,
+ * and with weight h the sums below are accumulated into the bins.  All output
+ * arrays must be zeroed by the caller:
+ *   1D  (nk):      modes1d, ksum1d, psum1d, p2sum1d (P L2(mu)), p4sum1d (P L4(mu))
+ *   2D  (nk*nmu):  modes2d, ksum2d, musum2d, psum2d   (only if nmu > 0)
+ * Returns 0, or -1 on bad arguments. */
+int oracle_bin(const double *F1, const double *F2, int N, double L, int p,
+               int compensated, double wsum, double kmin, double dk, int nk,
+               int nmu, int64_t *modes1d, double *ksum1d, double *psum1d,
+               double *p2sum1d, double *p4sum1d, int64_t *modes2d,
+               double *ksum2d, double *musum2d, double *psum2d)
+{
+    if (N < 2 || (N % 2) != 0 || L <= 0.0 || dk <= 0.0 || nk < 0 || nmu < 0)
+        return -1;
+    const int64_t NN = N, Nh = N / 2 + 1;
+    const double kF = (2.0 * M_PI) / L;
+    const double L3 = L * L * L;
+    for (int64_t i = 0; i < NN; ++i) {
+        int64_t ip = i < NN / 2 ? i : i - NN;       /* fftfreq */
+        for (int64_t j = 0; j < NN; ++j) {
+            int64_t jp = j < NN / 2 ? j : j - NN;
+            for (int64_t l = 0; l < Nh; ++l) {
+                int64_t m = ip * ip + jp * jp + l * l;
+                if (m == 0) continue;                /* DC is never binned */
+                int64_t b = oracle_kbin(m, L, kmin, dk);
+                if (b < 0 || b >= nk) continue;
+                double h = (l == 0 || l == NN / 2) ? 1.0 : 2.0;
+                int64_t idx = ((i * NN) + j) * Nh + l;
+                double re = F1[2 * idx], im = F1[2 * idx + 1];
+                if (F2) {
+                    double ph = M_PI * (double)(ip + jp + l) / (double)N;
+                    double c = cos(ph), s = sin(ph);
+                    double re2 = F2[2 * idx], im2 = F2[2 * idx + 1];
+                    re = 0.5 * (re + (re2 * c - im2 * s));
+                    im = 0.5 * (im + (re2 * s + im2 * c));
+                }
+                if (compensated) {
+                    double W = pow(sinc(M_PI * (double)ip / N), p) *
+                               pow(sinc(M_PI * (double)jp / N), p) *
+                               pow(sinc(M_PI * (double)l / N), p);
+                    re /= W;
+                    im /= W;
+                }
+                re /= wsum;
+                im /= wsum;
+                double P = L3 * (re * re + im * im);
+                double k = kF * sqrt((double)m);
+                double mu = (double)l / sqrt((double)m);
+                double mu2 = mu * mu;
+                double L2 = 0.5 * (3.0 * mu2 - 1.0);
+                double L4 = (35.0 * mu2 * mu2 - 30.0 * mu2 + 3.0) / 8.0;
+                modes1d[b] += (int64_t)h;
+                ksum1d[b] += h * k;
+                psum1d[b] += h * P;
+                p2sum1d[b] += h * P * L2;
+                p4sum1d[b] += h * P * L4;
+                if (nmu > 0) {
+                    int64_t q = oracle_mubin(m, l, nmu);
+                    int64_t bq = b * nmu + q;
+                    modes2d[bq] += (int64_t)h;
+                    ksum2d[bq] += h * k;
+                    musum2d[bq] += h * mu;
+                    psum2d[bq] += h * P;
+                }
+            }
+        }
+    }
+    return 0;
+}
