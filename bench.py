@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 FFT power-spectrum path; prints ONE JSON line.
+
+Workload (one step = one full power-spectrum evaluation of one catalog):
+1e7 objects Poisson-sampled from a log-normal field (P ~ k^-1.5, sigma^2 ~ 1
+at the cell scale) with a linear RSD displacement f = 0.75 along z, L = 1000
+Mpc/h, FP32 positions resident in HBM; TSC + interlacing on Nmesh = 512,
+compensated; (k, mu) bins dk = 0.005 to k_N with 10 mu bins and multipoles
+l = 0, 2, 4, shot noise subtracted.  A step runs pk_paint (tile sort + tile
+paint of both meshes), pk_compute (cuFFT r2c of both meshes, fused
+compensate/interlace/bin, reduce, finalize) and pk_result (host-visible
+result).  Each step is bracketed by CUDA events on the plan's stream; the L2
+is flushed (a 512 MB device write) between steps, outside the events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+N > 1 runs under torch.distributed.run: every rank evaluates its own
+independent catalog (weak scaling, no data-path collective); value = catalogs
+of all ranks / max-over-ranks device time.  --impl reference times the FP64
+CPU oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "P(k)/s + particles painted/s at Nmesh 512/2048, batched vs plain; p50/p99 latency"
+L_BOX, NMESH, NPART, DK, NMU = 1000.0, 512, 10_000_000, 0.005, 10
+WORKLOAD = ("lognormal 1e7 objects (P~k^-1.5, sigma^2~1, RSD f=0.75), L=1000 Mpc/h, FP32 positions, "
+            "TSC + interlacing, Nmesh=512, compensated, dk=0.005 to k_N (321 k bins) x 10 mu bins, "
+            "multipoles l=0,2,4, shot noise subtracted")
+ORACLE_PAINT_FRACTION = 8     # the CPU oracle paints 1/8 of the objects per step
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- clocks --
+class ClockSampler:
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                if self.uuid and parts[1] != self.uuid:
+                    continue
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        smax = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------ distributed --
+def dist_setup(n):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------- oracle leg --
+def oracle_step(pos64):
+    """One bounded oracle step on the host cores: paint 1/8 of the objects on
+    both interlaced meshes (scaled x8), both FP64 r2c FFTs and the full mode
+    loop at full size.  Returns the estimated seconds of one full evaluation."""
+    import numpy as np
+    import oracle
+    n = pos64.shape[0]
+    sub = pos64[: n // ORACLE_PAINT_FRACTION]
+    t0 = time.perf_counter()
+    m1 = oracle.paint(sub, None, L_BOX, NMESH, "tsc", 0.0)
+    m2 = oracle.paint(sub, None, L_BOX, NMESH, "tsc", 0.5)
+    t1 = time.perf_counter()
+    F1 = oracle.r2c(m1)
+    del m1
+    F2 = oracle.r2c(m2)
+    del m2
+    t2 = time.perf_counter()
+    oracle.bin_modes(F1, F2, L_BOX, "tsc", True, float(n), DK, nmu=NMU)
+    t3 = time.perf_counter()
+    return (t1 - t0) * ORACLE_PAINT_FRACTION + (t2 - t1) + (t3 - t2)
+
+
+def oracle_sample_text():
+    return ("per step: FP64 oracle paints 1/%d of the 1e7 objects on both TSC meshes (time x%d), "
+            "then both full 512^3 r2c FFTs and the full 512^2x257 mode loop" %
+            (ORACLE_PAINT_FRACTION, ORACLE_PAINT_FRACTION))
+
+
+def make_catalog(rank, device):
+    import synth
+    return synth.lognormal_catalog(NPART, L_BOX, NMESH, synth.seed_for(2, rank), device=device)
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    import torch
+    pos = make_catalog(0, "cuda" if torch.cuda.is_available() else "cpu").double().cpu().numpy()
+    for _ in range(args.warmup):
+        oracle_step(pos)
+    ts = [oracle_step(pos) for _ in range(args.steps)]
+    tot = sum(ts)
+    value = args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "P(k)/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nmesh": NMESH, "particles": NPART},
+        "cpu_baseline": {"value": value, "unit": "P(k)/s", "cores": 1, "kind": "oracle",
+                         "sample": oracle_sample_text()},
+        "e2e": {"value": value, "unit": "P(k)/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------- GPU leg --
+def traffic_record(kernel):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    src = os.path.join(ROOT, "paper_1712_05834_gb300", "csrc", "pk_kernels.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        with open(path) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel and parts[3] == sha:
+                    return float(parts[2])
+    except OSError:
+        pass
+    return None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    import paper_1712_05834_gb300 as pk
+    world, rank, local = dist_setup(args.gpus)
+    pk.build()
+    pk.load()
+    stream = torch.cuda.Stream()
+    pos = make_catalog(rank, "cuda")
+    torch.cuda.synchronize()
+    cfg = pk.make_config(L_BOX, NMESH, "tsc", interlaced=True, dk=DK, nmu=NMU, precision="f32")
+    with torch.cuda.stream(stream):
+        plan = pk.pk_plan(cfg, stream)
+        pk.pk_enable_timing(plan, True)
+        flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+        def step():
+            pk.pk_paint(plan, pos)
+            pk.pk_compute(plan)
+            return pk.pk_result(plan, 0)
+
+        for _ in range(max(args.warmup, 3)):
+            res = step()
+        torch.cuda.synchronize()
+        uuid = None
+        try:
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+        except Exception:
+            pass
+        clocks = ClockSampler(uuid)
+        clocks.start()
+        time.sleep(0.3)
+        barrier(world)
+        torch.cuda.synchronize()
+        launches0 = pk.pk_launch_count(plan)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        stages = {s: [] for s in pk.STAGES}
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)                      # L2 flush, outside the events
+            ev[k][0].record(stream)
+            res = step()
+            ev[k][1].record(stream)
+            st = pk.pk_stage_times(plan)
+            for s in pk.STAGES:
+                stages[s].append(st[s])
+        torch.cuda.synchronize()
+        barrier(world)
+        wall = time.perf_counter() - wall0
+        launches = pk.pk_launch_count(plan) - launches0
+        clk = clocks.stop()
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        total_s = max_over_ranks(sum(step_ms) / 1e3, world)
+
+        # e2e through the public API with host (pinned) buffers
+        host = pos.cpu().pin_memory()
+        e2e_steps = max(3, min(args.steps, 20))
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            pk.pk_paint(plan, host)
+            pk.pk_compute(plan)
+            res_e2e = pk.pk_result(plan, 0)
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+        pk.pk_destroy(plan)
+
+    if rank != 0:
+        return 0
+    K = args.steps
+    value = world * K / total_s
+    med = {s: statistics.median(v) for s, v in stages.items()}
+    nmodes = NMESH * NMESH * (NMESH // 2 + 1)
+    hbm, peak_kind = peaks()
+    # algorithmic bytes per launch
+    paint_bytes = NPART * 12 + 2 * NMESH ** 3 * 4            # xyz FP32 in + 2 FP32 meshes out
+    bin_bytes = 2 * nmodes * 8                               # 2 complex64 meshes read
+    roof = {
+        "paint": {"bound": "hbm", "achieved": paint_bytes / (med["sort"] + med["paint"]) / 1e6,
+                  "stage_ms": med["sort"] + med["paint"], "bytes": paint_bytes,
+                  "kernels": "k_tile_count + k_scan_* + k_tile_scatter + k_paint_tiles"},
+        "bin": {"bound": "hbm", "achieved": bin_bytes / med["bin"] / 1e6, "stage_ms": med["bin"],
+                "bytes": bin_bytes, "kernels": "k_bin"},
+    }
+    for r in roof.values():
+        r["peak"] = hbm
+        r["frac"] = r["achieved"] / hbm
+    dom = "paint" if roof["paint"]["stage_ms"] >= roof["bin"]["stage_ms"] else "bin"
+    dk_name = "k_paint_tiles" if dom == "paint" else "k_bin"
+    rl = {"bound": "hbm", "achieved": roof[dom]["achieved"], "peak": hbm, "unit": "GB/s",
+          "frac": roof[dom]["frac"], "traffic": traffic_record(dk_name),
+          "kernel": roof[dom]["kernels"], "peak_kind": peak_kind,
+          "algorithmic_bytes_per_launch": roof[dom]["bytes"]}
+    res_bytes = 8 * (len(res["power"]) * 4 + res["power2d"].size + 4)
+    line = {
+        "metric": METRIC, "value": value, "unit": "P(k)/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nmesh": NMESH, "particles": NPART,
+                   "form": "FP32 mesh, int64 fixed-point paint, FP64 bin sums",
+                   "l2": "flushed between steps (512 MB device write outside the timed events)",
+                   "parallelism": "replicas" if world == 1 else "dp%d (independent catalogs)" % world},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+        "particles_painted_per_s": NPART / ((med["sort"] + med["paint"]) / 1e3),
+        "modes_binned_per_s": 2 * nmodes / (med["bin"] / 1e3),
+        "stage_ms_median": med,
+        "fft_ms": med["fft"],
+        "roofline": rl,
+        "rooflines": roof,
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "e2e": {"value": world * e2e_steps / e2e_s, "unit": "P(k)/s",
+                "h2d_bytes_per_step": int(NPART * 12), "d2h_bytes_per_step": int(res_bytes)},
+        "wall_s_timed": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        pos64 = pos.double().cpu().numpy()
+        t = oracle_step(pos64)
+        line["cpu_baseline"] = {"value": 1.0 / t, "unit": "P(k)/s", "cores": 1, "kind": "oracle",
+                                "sample": oracle_sample_text()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

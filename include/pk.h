@@ -1,0 +1,216 @@
+/*
+ * pk.h -- C ABI of the GB300 FFT power-spectrum library (libpk.so).
+ *
+ * The library computes the FFTPower estimator of nbodykit (Hand, Feng et al.,
+ * arXiv:1712.05834) on one GPU:
+ *
+ *   paint     objects -> mesh with a CIC / TSC / PCS window, optionally a
+ *             second mesh shifted by half a cell (interlacing)      Sec. 3.3.1-3.3.2
+ *   r2c FFT   real mesh -> complex half grid (cuFFT)                Sec. 3.3.1
+ *   compensate + interlace: divide by prod_i sinc^p(pi k_i / 2 k_N),
+ *             average the two meshes with the half-cell phase       Eq. window-deconvolution
+ *   bin       |delta(k)|^2 into k bins, (k, mu) bins about the z axis,
+ *             Legendre multipoles l = 0, 2, 4, shot noise removed   Sec. 3.4.1
+ *
+ * Plain C types only.  Every call returns a pk_status; no call aborts or
+ * throws.  A failed call leaves a message retrievable with pk_last_error().
+ *
+ * Conventions (fixed here because the paper leaves them open):
+ *   - mesh node c sits at c * H, H = L / N; positions are wrapped into [0, L);
+ *   - axis order (x, y, z) with z fastest in memory; the r2c axis and the line
+ *     of sight are both z;
+ *   - the interlaced mesh is painted at x + H/2 on all three axes and its
+ *     transform multiplied by exp(+i (kx + ky + kz) H / 2) before averaging;
+ *   - delta(k) = F~(k) / sum(w); P = L^3 |delta(k)|^2;
+ *   - shot noise P_shot = L^3 sum(w^2) / sum(w)^2 (= 1 / nbar for unit weights),
+ *     subtracted from P(k), P(k, mu) and P_0 only;
+ *   - the DC mode is never binned; the stored half grid carries weight h = 1 on
+ *     the l = 0 and l = N/2 planes and h = 2 elsewhere; x, y indices follow
+ *     numpy fftfreq;
+ *   - k bin b = floor((kF sqrt(m) - kmin) / dk), FP64, kF = (2 pi) / L,
+ *     m = i'^2 + j'^2 + l^2; nk = floor((kmax - kmin) / dk); a mode is binned
+ *     iff 0 <= b < nk; kmax <= 0 selects k_N = (pi N) / L;
+ *   - mu = l / sqrt(m); mu bin q = largest q with q^2 m <= nmu^2 l^2, clamped
+ *     to nmu - 1 (edges linspace(0, 1, nmu + 1), lower edge inclusive);
+ *   - P_l(k) = (2l + 1) sum h P L_l(mu) / sum h, taken over the 1D k bins.
+ */
+#ifndef PK_H
+#define PK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pk_plan_s *pk_plan_t;
+
+typedef enum {
+    PK_OK = 0,
+    PK_EINVAL = 1,     /* an argument is out of range; nothing was launched    */
+    PK_ENOMEM = 2,     /* a device or pinned host allocation failed            */
+    PK_ECUDA = 3,      /* a CUDA runtime call failed (message has the string)  */
+    PK_ECUFFT = 4,     /* a cuFFT call failed                                  */
+    PK_EOVERFLOW = 5,  /* fixed-point paint headroom exceeded: lower the scale */
+    PK_ETIMEOUT = 6,   /* a bounded device wait gave up                        */
+    PK_ESTATE = 7      /* call out of order (e.g. compute before paint)        */
+} pk_status;
+
+typedef enum { PK_CIC = 2, PK_TSC = 3, PK_PCS = 4 } pk_window;   /* value = p */
+
+/* Position layouts accepted by pk_paint. */
+typedef enum {
+    PK_F32 = 0,    /* n x 3 float, xyz packed (12 bytes per object)             */
+    PK_F64 = 1,    /* n x 3 double, xyz packed (24 bytes per object)            */
+    PK_F32X4 = 2   /* n x 4 float, xyzw with w the weight; 16-byte aligned      */
+} pk_dtype;
+
+/* Mesh / transform precision.  Both paint into int64 fixed point (so the
+ * mesh is bit-identical run to run) and sum bins in FP64. */
+typedef enum {
+    PK_MESH_F32 = 0,   /* FP32 mesh, cuFFT R2C, FP32 per-mode arithmetic        */
+    PK_MESH_F64 = 1    /* FP64 mesh, cuFFT D2Z, FP64 per-mode arithmetic        */
+} pk_precision;
+
+typedef struct {
+    double box_size;        /* L > 0                                             */
+    int nmesh;              /* N: even, 4 <= N <= 4096                           */
+    int window;             /* pk_window                                         */
+    int interlaced;         /* 0 / 1                                             */
+    int compensated;        /* 0 / 1: divide by prod_i sinc^p                    */
+    double kmin;            /* >= 0                                              */
+    double kmax;            /* <= 0 selects k_N                                  */
+    double dk;              /* > 0                                               */
+    int nmu;                /* 0: 1D bins only; >= 1: (k, mu) bins too           */
+    unsigned poles_mask;    /* bit0 l=0, bit1 l=2, bit2 l=4                      */
+    int los_axis;           /* must be 2 (z)                                     */
+    int precision;          /* pk_precision                                      */
+    int subtract_shot;      /* 0 / 1                                             */
+    int fixed_scale_log2;   /* S: one weight unit = 2^S; 0 selects 32; 1..40     */
+    int batch;              /* catalogs per plan (separate meshes); 0 -> 1       */
+    int tile;               /* paint tile edge in cells; 0 -> automatic          */
+} pk_config;
+
+/* Result of one catalog.  All pointers are host memory owned by the plan and
+ * stay valid until the next pk_compute or pk_destroy on that plan.  Arrays
+ * of length nk * nmu are row-major [k bin][mu bin].  Empty bins hold NaN. */
+typedef struct {
+    int nk, nmu, npoles;          /* npoles = 3: rows l = 0, 2, 4                 */
+    const double *k_edges;        /* nk + 1                                       */
+    const double *mu_edges;       /* nmu + 1 (NULL if nmu == 0)                   */
+    const double *k_mean;         /* nk: mode-weighted mean |k| per k bin         */
+    const double *pk;             /* nk: P(k), shot noise removed if requested    */
+    const double *poles;          /* 3 * nk: P_0, P_2, P_4 (rows not in the mask
+                                     are NaN)                                      */
+    const uint64_t *modes;        /* nk: weighted mode counts (full-grid count)   */
+    const double *k_mean2d;       /* nk * nmu                                     */
+    const double *mu_mean2d;      /* nk * nmu                                     */
+    const double *pkmu;           /* nk * nmu: P(k, mu)                           */
+    const uint64_t *modes2d;      /* nk * nmu                                     */
+    double shot_noise;            /* L^3 sum(w^2) / sum(w)^2                      */
+    double wsum, w2sum;           /* sum(w), sum(w^2) of the painted objects      */
+} pk_result_view;
+
+/* Fill *cfg with defaults: L = 1000, N = 256, CIC, not interlaced, compensated,
+ * kmin = 0, kmax = k_N, dk = 2 kF, nmu = 0, all poles, z line of sight, FP32
+ * mesh, shot noise subtracted, S = 32, batch 1, automatic tile. */
+void pk_config_default(pk_config *cfg);
+
+/* Create a plan: validates cfg, allocates the meshes (in-place r2c layout,
+ * N x N x 2(N/2+1) reals per mesh, (1 + interlaced) meshes per catalog), the
+ * cuFFT plan, the bin tables and result buffers, and computes the geometry-only
+ * bin data (mode counts, mean k, mean mu) on the device.  All work of the plan
+ * is issued on `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
+ * The device is the one current at this call.  On success *out owns
+ * everything; release it with pk_destroy.
+ * Errors: PK_EINVAL (bad config, message says which field), PK_ENOMEM, PK_ECUDA,
+ * PK_ECUFFT.  On error *out is NULL and nothing is leaked. */
+pk_status pk_plan(const pk_config *cfg, void *cuda_stream, pk_plan_t *out);
+
+/* Paint n objects onto the mesh(es) of catalog 0 (Sec. 3.3.1, Eq. painting:
+ * F = [1 + delta'] V with V = 1 and per-object weights W).
+ *   pos      n objects in layout `dtype`, device or host memory (host memory is
+ *            copied to the device on the plan's stream inside the call);
+ *   weights  n floats (device or host) or NULL for unit weights; must be NULL
+ *            with PK_F32X4, whose 4th component is the weight;
+ *   accumulate 0: the catalog replaces the mesh; 1: it is added (the mesh must
+ *            not have been transformed since the last paint).
+ * Caller keeps ownership of pos and weights; they are read on the plan's
+ * stream and may be reused once the stream has passed this call.  The call
+ * synchronizes the stream once (to size the tile-sorted copy of the objects).
+ * Errors: PK_EINVAL (n < 0, bad dtype, misaligned PK_F32X4), PK_ESTATE
+ * (accumulate onto a transformed mesh), PK_ENOMEM, PK_ECUDA. */
+pk_status pk_paint(pk_plan_t plan, const void *pos, int dtype,
+                   const float *weights, int64_t n, int accumulate);
+
+/* Batched paint: catalogs 0 .. nitems-1 of a plan created with batch >= nitems.
+ * pos / weights hold the catalogs back to back; offsets (host memory, nitems+1
+ * entries, offsets[0] = 0, non-decreasing) delimit them.  Same layout rules,
+ * ownership and errors as pk_paint, with accumulate = 0. */
+pk_status pk_paint_many(pk_plan_t plan, const void *pos, int dtype,
+                        const float *weights, const int64_t *offsets, int nitems);
+
+/* Transform, compensate, interlace and bin every painted catalog of the plan
+ * (Sec. 3.4.1 with Eq. window-deconvolution).  Asynchronous on the plan's
+ * stream; the results are copied to plan-owned host memory and become
+ * readable through pk_result.  Errors: PK_ESTATE (a catalog is not painted),
+ * PK_ECUFFT, PK_ECUDA. */
+pk_status pk_compute(pk_plan_t plan);
+
+/* Wait for the last pk_compute and describe catalog `item`'s result.
+ * Errors: PK_ESTATE (no compute yet), PK_EINVAL (item out of range),
+ * PK_EOVERFLOW (fixed-point headroom exceeded while painting), PK_ECUDA. */
+pk_status pk_result(pk_plan_t plan, int item, pk_result_view *out);
+
+/* Copy painted mesh `mesh` (0, or 1 = the interlaced mesh) of catalog `item`
+ * into dst as a dense N x N x N array (z fastest) of the plan's precision
+ * (float for PK_MESH_F32, double for PK_MESH_F64): the painted field F of
+ * Sec. 3.3.1, in units of the object weights.  dst may be host or device
+ * memory of at least N^3 elements; the call waits for the copy.  Valid between
+ * a paint and the next pk_compute.  Errors: PK_ESTATE (mesh already
+ * transformed or never painted), PK_EINVAL (item / mesh out of range), PK_ECUDA. */
+pk_status pk_mesh(pk_plan_t plan, int item, int mesh, void *dst);
+
+/* Stages whose device time pk_stage_times reports. */
+typedef enum {
+    PK_STAGE_SORT = 0,    /* tile count + scan + scatter (pk_paint)             */
+    PK_STAGE_PAINT = 1,   /* shared-memory tile paint (pk_paint)                */
+    PK_STAGE_FFT = 2,     /* cuFFT r2c of every mesh (pk_compute)               */
+    PK_STAGE_BIN = 3,     /* compensate + interlace + bin (pk_compute)          */
+    PK_STAGE_FINAL = 4,   /* histogram reduce + normalize + multipoles          */
+    PK_NSTAGES = 5
+} pk_stage;
+
+/* Turn per-stage timing on (1) or off (0).  When on, pk_paint and pk_compute
+ * record CUDA events on the plan's stream around each stage.  No effect on
+ * results. */
+pk_status pk_enable_timing(pk_plan_t plan, int on);
+
+/* Device milliseconds of each stage (PK_NSTAGES doubles) of the last pk_paint
+ * and pk_compute with timing on; waits for those events.  Stages not run are
+ * 0.  Errors: PK_ESTATE (timing off), PK_ECUDA. */
+pk_status pk_stage_times(pk_plan_t plan, double *ms);
+
+/* Number of the library's own kernels launched on this plan since pk_plan
+ * (plan-time geometry kernels included; cuFFT's kernels and memsets not). */
+long long pk_launch_count(pk_plan_t plan);
+
+/* Free everything the plan owns (waits for its stream).  NULL is a no-op. */
+pk_status pk_destroy(pk_plan_t plan);
+
+/* Static string naming a status. */
+const char *pk_status_string(pk_status status);
+
+/* Message of the last failed call on this plan ("" if none).  Valid until the
+ * next call on the plan. */
+const char *pk_last_error(pk_plan_t plan);
+
+/* Message of the last failed pk_plan on this thread ("" if none). */
+const char *pk_plan_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PK_H */

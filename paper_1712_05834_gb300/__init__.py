@@ -1,0 +1,322 @@
+"""GB300 FFT power-spectrum path: Python binding of ``libpk.so``.
+
+The estimator is nbodykit's FFTPower (Hand, Feng et al., arXiv:1712.05834):
+paint a catalog onto a mesh with a CIC / TSC / PCS window, optionally
+interlaced (Sec. 3.3.1-3.3.2), r2c FFT, window compensation
+(Eq. window-deconvolution), and |delta(k)|^2 binned in k, (k, mu) and Legendre
+multipoles (Sec. 3.4.1).  Every step runs in the CUDA kernels of ``libpk.so``;
+this module only marshals arguments to the C ABI declared in
+``include/pk.h`` and keeps its names: ``pk_plan``, ``pk_paint``,
+``pk_paint_many``, ``pk_compute``, ``pk_result``, ``pk_mesh``, ``pk_destroy``.
+
+There is no fallback: if the library is missing or no GPU is present the calls
+raise.  ``build()`` compiles the library in-tree (nvcc, sm_103a).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from .build import LIB as LIB_PATH
+from .build import build
+
+__all__ = [
+    "PK_CIC", "PK_TSC", "PK_PCS", "PK_F32", "PK_F64", "PK_F32X4", "PK_MESH_F32", "PK_MESH_F64",
+    "PkError", "pk_config", "pk_config_default", "make_config", "pk_plan", "pk_paint",
+    "pk_paint_many", "pk_compute", "pk_result", "pk_mesh", "pk_destroy", "pk_status_string",
+    "pk_last_error", "pk_enable_timing", "pk_stage_times", "pk_launch_count", "FFTPower", "load",
+    "build",
+]
+
+PK_OK, PK_EINVAL, PK_ENOMEM, PK_ECUDA, PK_ECUFFT, PK_EOVERFLOW, PK_ETIMEOUT, PK_ESTATE = range(8)
+PK_CIC, PK_TSC, PK_PCS = 2, 3, 4
+PK_F32, PK_F64, PK_F32X4 = 0, 1, 2
+PK_MESH_F32, PK_MESH_F64 = 0, 1
+WINDOWS = {"cic": PK_CIC, "tsc": PK_TSC, "pcs": PK_PCS}
+EXPORTED = ["pk_config_default", "pk_plan", "pk_paint", "pk_paint_many", "pk_compute",
+            "pk_result", "pk_mesh", "pk_destroy", "pk_status_string", "pk_last_error",
+            "pk_plan_error", "pk_enable_timing", "pk_stage_times", "pk_launch_count"]
+STAGES = ["sort", "paint", "fft", "bin", "final"]
+
+
+class pk_config(ctypes.Structure):
+    _fields_ = [
+        ("box_size", ctypes.c_double), ("nmesh", ctypes.c_int), ("window", ctypes.c_int),
+        ("interlaced", ctypes.c_int), ("compensated", ctypes.c_int), ("kmin", ctypes.c_double),
+        ("kmax", ctypes.c_double), ("dk", ctypes.c_double), ("nmu", ctypes.c_int),
+        ("poles_mask", ctypes.c_uint), ("los_axis", ctypes.c_int), ("precision", ctypes.c_int),
+        ("subtract_shot", ctypes.c_int), ("fixed_scale_log2", ctypes.c_int), ("batch", ctypes.c_int),
+        ("tile", ctypes.c_int),
+    ]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_up = ctypes.POINTER(ctypes.c_uint64)
+
+
+class pk_result_view(ctypes.Structure):
+    _fields_ = [
+        ("nk", ctypes.c_int), ("nmu", ctypes.c_int), ("npoles", ctypes.c_int),
+        ("k_edges", _dp), ("mu_edges", _dp), ("k_mean", _dp), ("pk", _dp), ("poles", _dp),
+        ("modes", _up), ("k_mean2d", _dp), ("mu_mean2d", _dp), ("pkmu", _dp), ("modes2d", _up),
+        ("shot_noise", ctypes.c_double), ("wsum", ctypes.c_double), ("w2sum", ctypes.c_double),
+    ]
+
+
+class PkError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (pk_status_string(status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load libpk.so (built by ``build()``); raises if it is not there."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libpk.so is not built: call paper_1712_05834_gb300.build() first")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        lib.pk_config_default.argtypes = [ctypes.POINTER(pk_config)]
+        lib.pk_config_default.restype = None
+        lib.pk_plan.argtypes = [ctypes.POINTER(pk_config), vp, ctypes.POINTER(vp)]
+        lib.pk_plan.restype = i
+        lib.pk_paint.argtypes = [vp, vp, i, vp, i64, i]
+        lib.pk_paint.restype = i
+        lib.pk_paint_many.argtypes = [vp, vp, i, vp, ctypes.POINTER(ctypes.c_int64), i]
+        lib.pk_paint_many.restype = i
+        lib.pk_compute.argtypes = [vp]
+        lib.pk_compute.restype = i
+        lib.pk_result.argtypes = [vp, i, ctypes.POINTER(pk_result_view)]
+        lib.pk_result.restype = i
+        lib.pk_mesh.argtypes = [vp, i, i, vp]
+        lib.pk_mesh.restype = i
+        lib.pk_destroy.argtypes = [vp]
+        lib.pk_destroy.restype = i
+        lib.pk_status_string.argtypes = [i]
+        lib.pk_status_string.restype = ctypes.c_char_p
+        lib.pk_last_error.argtypes = [vp]
+        lib.pk_last_error.restype = ctypes.c_char_p
+        lib.pk_plan_error.argtypes = []
+        lib.pk_plan_error.restype = ctypes.c_char_p
+        lib.pk_enable_timing.argtypes = [vp, i]
+        lib.pk_enable_timing.restype = i
+        lib.pk_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        lib.pk_stage_times.restype = i
+        lib.pk_launch_count.argtypes = [vp]
+        lib.pk_launch_count.restype = ctypes.c_longlong
+        _lib = lib
+    return _lib
+
+
+def pk_status_string(status: int) -> str:
+    return load().pk_status_string(int(status)).decode()
+
+
+def pk_last_error(plan) -> str:
+    return load().pk_last_error(plan).decode()
+
+
+def _check(status, plan=None):
+    if status != PK_OK:
+        msg = load().pk_plan_error().decode() if plan is None else pk_last_error(plan)
+        raise PkError(status, msg)
+
+
+def pk_config_default() -> pk_config:
+    c = pk_config()
+    load().pk_config_default(ctypes.byref(c))
+    return c
+
+
+def make_config(box_size, nmesh, window="cic", interlaced=False, compensated=True, dk=None,
+                kmin=0.0, kmax=None, nmu=0, poles=(0, 2, 4), precision="f32",
+                subtract_shot=True, fixed_scale_log2=0, batch=1, tile=0) -> pk_config:
+    """pk_config from keyword arguments that follow the paper's ``to_mesh`` /
+    ``FFTPower`` options (Sec. 3.3.2, Sec. 3.4.1).  dk defaults to 2 kF."""
+    c = pk_config_default()
+    c.box_size = float(box_size)
+    c.nmesh = int(nmesh)
+    c.window = WINDOWS[window] if isinstance(window, str) else int(window)
+    c.interlaced = int(bool(interlaced))
+    c.compensated = int(bool(compensated))
+    c.kmin = float(kmin)
+    c.kmax = 0.0 if kmax is None else float(kmax)
+    c.dk = float(dk) if dk is not None else 2.0 * (2.0 * math.pi) / float(box_size)
+    c.nmu = int(nmu)
+    c.poles_mask = sum({0: 1, 2: 2, 4: 4}[ell] for ell in poles)
+    c.los_axis = 2
+    c.precision = {"f32": PK_MESH_F32, "f64": PK_MESH_F64}[precision] if isinstance(precision, str) else int(precision)
+    c.subtract_shot = int(bool(subtract_shot))
+    c.fixed_scale_log2 = int(fixed_scale_log2)
+    c.batch = int(batch)
+    c.tile = int(tile)
+    return c
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def pk_plan(cfg: pk_config, stream=None):
+    """Create a plan (device = the current CUDA device).  ``stream`` is a
+    torch.cuda.Stream, a raw cudaStream_t integer, or None (default stream)."""
+    h = ctypes.c_void_p()
+    _check(load().pk_plan(ctypes.byref(cfg), _stream_ptr(stream), ctypes.byref(h)))
+    return h
+
+
+def _array_info(a):
+    """(pointer, dtype code, n) of a position array: torch tensor or numpy array."""
+    shape = tuple(a.shape)
+    if len(shape) != 2 or shape[1] not in (3, 4):
+        raise ValueError("positions must have shape (n, 3) or (n, 4)")
+    if hasattr(a, "data_ptr"):                      # torch tensor
+        if not a.is_contiguous():
+            raise ValueError("positions must be contiguous")
+        name = str(a.dtype)
+        ptr = a.data_ptr()
+    else:
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("positions must be C-contiguous")
+        name = str(a.dtype)
+        ptr = a.ctypes.data
+    if shape[1] == 4:
+        if "float32" not in name:
+            raise ValueError("(n, 4) positions must be float32 xyzw")
+        return ptr, PK_F32X4, shape[0]
+    if "float32" in name:
+        return ptr, PK_F32, shape[0]
+    if "float64" in name:
+        return ptr, PK_F64, shape[0]
+    raise ValueError("positions must be float32 or float64")
+
+
+def _weights_ptr(w, n):
+    if w is None:
+        return None
+    if tuple(w.shape) != (n,):
+        raise ValueError("weights must have shape (n,)")
+    if hasattr(w, "data_ptr"):
+        if str(w.dtype) != "torch.float32" or not w.is_contiguous():
+            raise ValueError("weights must be contiguous float32")
+        return w.data_ptr()
+    if w.dtype != np.float32 or not w.flags["C_CONTIGUOUS"]:
+        raise ValueError("weights must be contiguous float32")
+    return w.ctypes.data
+
+
+def pk_paint(plan, pos, weights=None, accumulate=False):
+    """Paint one catalog (device or host array) onto the plan's mesh(es)."""
+    ptr, code, n = _array_info(pos)
+    _check(load().pk_paint(plan, ptr, code, _weights_ptr(weights, n), n, int(bool(accumulate))), plan)
+
+
+def pk_paint_many(plan, pos, offsets, weights=None):
+    """Paint catalogs stored back to back; offsets has nitems + 1 entries."""
+    ptr, code, n = _array_info(pos)
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    if off[-1] != n:
+        raise ValueError("offsets[-1] must equal the number of objects")
+    _check(load().pk_paint_many(plan, ptr, code, _weights_ptr(weights, n),
+                                off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(off) - 1), plan)
+
+
+def pk_compute(plan):
+    _check(load().pk_compute(plan), plan)
+
+
+def _arr(ptr, n, dtype=np.float64):
+    if not ptr or n == 0:
+        return None
+    return np.ctypeslib.as_array(ptr, shape=(n,)).astype(dtype, copy=True)
+
+
+def pk_result(plan, item=0) -> dict:
+    """Result of catalog ``item`` of the last compute, copied into numpy arrays."""
+    v = pk_result_view()
+    _check(load().pk_result(plan, int(item), ctypes.byref(v)), plan)
+    nk, nmu = v.nk, v.nmu
+    out = {
+        "nk": nk, "nmu": nmu,
+        "k_edges": _arr(v.k_edges, nk + 1),
+        "k": _arr(v.k_mean, nk),
+        "power": _arr(v.pk, nk),
+        "poles": _arr(v.poles, 3 * nk).reshape(3, nk),
+        "modes": _arr(v.modes, nk, np.int64),
+        "shot_noise": v.shot_noise, "wsum": v.wsum, "w2sum": v.w2sum,
+    }
+    if nmu > 0:
+        out["mu_edges"] = _arr(v.mu_edges, nmu + 1)
+        out["k2d"] = _arr(v.k_mean2d, nk * nmu).reshape(nk, nmu)
+        out["mu2d"] = _arr(v.mu_mean2d, nk * nmu).reshape(nk, nmu)
+        out["power2d"] = _arr(v.pkmu, nk * nmu).reshape(nk, nmu)
+        out["modes2d"] = _arr(v.modes2d, nk * nmu, np.int64).reshape(nk, nmu)
+    return out
+
+
+def pk_mesh(plan, item, mesh, nmesh, f64=False):
+    """Dense (N, N, N) numpy copy of a painted mesh (before pk_compute)."""
+    out = np.empty((nmesh, nmesh, nmesh), dtype=np.float64 if f64 else np.float32)
+    _check(load().pk_mesh(plan, int(item), int(mesh), out.ctypes.data), plan)
+    return out
+
+
+def pk_enable_timing(plan, on=True):
+    _check(load().pk_enable_timing(plan, int(bool(on))), plan)
+
+
+def pk_stage_times(plan) -> dict:
+    """Device ms per stage of the last timed pk_paint / pk_compute."""
+    ms = (ctypes.c_double * len(STAGES))()
+    _check(load().pk_stage_times(plan, ms), plan)
+    return dict(zip(STAGES, list(ms)))
+
+
+def pk_launch_count(plan) -> int:
+    return int(load().pk_launch_count(plan))
+
+
+def pk_destroy(plan):
+    if plan:
+        _check(load().pk_destroy(plan))
+
+
+class FFTPower:
+    """Plan-owning convenience wrapper: ``FFTPower(cfg).run(pos, weights)``."""
+
+    def __init__(self, cfg: pk_config, stream=None):
+        self.cfg = cfg
+        self.plan = pk_plan(cfg, stream)
+
+    def run(self, pos, weights=None):
+        pk_paint(self.plan, pos, weights)
+        pk_compute(self.plan)
+        return pk_result(self.plan, 0)
+
+    def close(self):
+        if self.plan:
+            pk_destroy(self.plan)
+            self.plan = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,92 @@
+// pk_internal.h -- declarations shared by the two translation units of
+// libpk.so (host API in pk_api.cu, kernels in pk_kernels.cu).  Not installed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pk.h"
+
+namespace pk {
+
+// Geometry of the tile-sorted paint (Sec. 3.3.1 painting, Sec. 3.3.2 windows).
+// The mesh is cut into cubic tiles of T^3 cells; an object is copied into every
+// tile that any of its window nodes (on either interlaced mesh) falls in, with
+// its position stored relative to that tile's origin.  Cells [floor(s)+lo,
+// floor(s)+hi] along each axis cover the support of both meshes.
+struct PaintGeom {
+    float invH;         // N / L in FP32
+    double invHd;       // N / L in FP64
+    int N;              // cells per side
+    int T;              // tile edge (divides N)
+    int ntx;            // tiles per side = N / T
+    int lo, hi;         // reach of the window support relative to floor(s)
+    long long ntiles;   // ntx^3 tiles per catalog
+};
+
+// Geometry of the fused compensate + interlace + bin pass (Sec. 3.4.1).
+struct BinGeom {
+    int N, Nh;              // Nh = N/2 + 1 stored z modes
+    int nk, nmu;            // k bins, mu bins (nmu = 0: 1D only)
+    int twod, poles;        // accumulate (k, mu) sums / mu^2, mu^4 sums
+    int hbase;              // first pole slot in the per-CTA histogram
+    int nh;                 // histogram length
+    float kscale, koff;     // bin estimate: sqrt(m) * kscale - koff
+    int mlo, mhi;           // binned modes have mlo <= m < mhi (and m != 0)
+    long long modes;        // stored modes per mesh: N * N * Nh
+};
+
+struct FinalGeom {
+    int nk, nmu, twod, poles, hbase, nh;
+    unsigned poles_mask;
+    int subtract_shot;
+    double L3;              // L^3
+    double headroom;        // 2^(62 - S): largest sum |w| with int64 cells safe
+    int RL;                 // doubles per item in the result block
+};
+
+// Offsets inside one item's FP64 result block.
+struct ResultLayout {
+    int pk, poles, pkmu, shot, wsum, w2sum, flags, total;
+};
+ResultLayout result_layout(int nk, int nmu);
+
+// ---- launchers (pk_kernels.cu); all asynchronous on `st` ----
+cudaError_t launch_tile_count(const void *pos, int dtype, const float *w, const int64_t *item_off,
+                              int nitems, int64_t max_n, const PaintGeom &g, uint32_t *count,
+                              double *wsums, cudaStream_t st);
+cudaError_t launch_scan(const uint32_t *count, int64_t n, int64_t *off, int64_t *block_tmp,
+                        cudaStream_t st);
+cudaError_t launch_tile_scatter(const void *pos, int dtype, const float *w,
+                                const int64_t *item_off, int nitems, int64_t max_n,
+                                const PaintGeom &g, uint32_t *count, const int64_t *off,
+                                float4 *sorted, int *err, cudaStream_t st);
+cudaError_t launch_paint_tiles(const float4 *sorted, const int64_t *off, int nitems,
+                               const PaintGeom &g, int window, int nmesh, int S, int f64,
+                               void *mesh, long long item_stride, long long mesh_stride,
+                               int accumulate, cudaStream_t st);
+size_t paint_smem_bytes(int T, int nmesh);
+
+cudaError_t launch_bin(const void *mesh, int f64, int interlaced, long long item_stride_c,
+                       long long mesh_stride_c, int nitems, int ctas_per_item,
+                       const BinGeom &g, const void *cw, const void *ph, const int *kedge,
+                       void *partial, cudaStream_t st);
+size_t bin_smem_bytes(const BinGeom &g, int f64);
+int bin_ctas_per_sm(const BinGeom &g, int f64, int interlaced);
+int bin_threads();
+
+cudaError_t launch_bin_reduce(const void *partial, int f64, int G, int nh, int nitems,
+                              double *sums, cudaStream_t st);
+cudaError_t launch_finalize(const double *sums, const unsigned long long *modes1d,
+                            const unsigned long long *modes2d, const double *wsums, const int *err,
+                            const FinalGeom &f, int nitems, double *res, cudaStream_t st);
+
+cudaError_t launch_geom_hist(const BinGeom &g, unsigned long long *H, unsigned long long *HL,
+                             cudaStream_t st);
+cudaError_t launch_geom_finalize(const BinGeom &g, const int *kedge, double kF,
+                                 const unsigned long long *H, const unsigned long long *HL,
+                                 unsigned long long *modes1d, double *kmean1d,
+                                 unsigned long long *modes2d, double *kmean2d,
+                                 double *mumean2d, cudaStream_t st);
+
+}  // namespace pk

@@ -1,0 +1,145 @@
+"""Seeded synthetic catalogs for tests and benchmarks.
+
+Shared by the oracle side (tests) and the CUDA side (tests, bench).  Holds none
+of the estimator's arithmetic (no painting, no windows, no binning): it only
+draws object positions with the structure of the paper's workloads --
+uniform random catalogs, Poisson-sampled log-normal fields with a linear
+redshift-space displacement (the kind of LogNormalCatalog the paper's tests
+and benchmarks use, Sec. 3.2 and Sec. 3.3.2) and Zel'dovich-displaced
+lattices.  Gaussian fields are drawn with torch (CPU or CUDA) from a seeded
+generator; positions come back as torch tensors on the requested device.
+
+Gaussian field convention: for white noise W on an N^3 grid (E|W~|^2 = N^3),
+G~(n) = W~(n) sqrt(P(k) N^3 / L^3) gives a grid field whose variance is
+(1/L^3) sum_{k != 0} P(k).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+SEED_BASE = 20171215
+
+
+def seed_for(config: int, mock: int = 0) -> int:
+    """Seed of mock `mock` of workload `config`: 20171215 + 1000 config + mock."""
+    return SEED_BASE + 1000 * int(config) + int(mock)
+
+
+def uniform_catalog(n: int, box_size: float, seed: int, dtype=np.float64) -> np.ndarray:
+    """n objects uniform in [0, L)^3 (numpy PCG64), shape (n, 3)."""
+    rng = np.random.default_rng(seed)
+    return (rng.random((n, 3)) * box_size).astype(dtype)
+
+
+def _kgrid(ng: int, box_size: float, device):
+    kf = 2.0 * math.pi / box_size
+    f = torch.fft.fftfreq(ng, d=1.0 / ng, device=device, dtype=torch.float64) * kf
+    fz = torch.fft.rfftfreq(ng, d=1.0 / ng, device=device, dtype=torch.float64) * kf
+    return f[:, None, None], f[None, :, None], fz[None, None, :]
+
+
+def gaussian_field_k(ng: int, box_size: float, slope: float, seed: int, device="cpu",
+                     amp: float | None = None, variance: float = 1.0):
+    """Half-grid transform G~ of a Gaussian field with P(k) = A k^slope.
+
+    If amp is None, A is set so the grid variance (1/L^3) sum_{k!=0} P(k)
+    equals `variance`.  Returns (G~ complex64 on device, A)."""
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    w = torch.randn((ng, ng, ng), generator=gen, device=device, dtype=torch.float32)
+    wk = torch.fft.rfftn(w)
+    del w
+    kx, ky, kz = _kgrid(ng, box_size, device)
+    k2 = kx * kx + ky * ky + kz * kz
+    k2[0, 0, 0] = 1.0
+    shape = (k2 ** (0.5 * slope))
+    shape[0, 0, 0] = 0.0
+    if amp is None:
+        # full-grid sum of k^slope: the half grid counts planes 0 and ng/2 once
+        h = torch.full((ng // 2 + 1,), 2.0, dtype=torch.float64, device=device)
+        h[0] = 1.0
+        if ng % 2 == 0:
+            h[-1] = 1.0
+        total = float((shape * h[None, None, :]).sum())
+        amp = variance * box_size ** 3 / total
+    scale = torch.sqrt(amp * shape * (ng ** 3) / box_size ** 3).to(torch.float32)
+    return wk * scale, amp
+
+
+def _displacement(gk, box_size: float, axis: int):
+    """Linear displacement psi_a = IFFT(i k_a / k^2 G~) on the grid (Mpc/h)."""
+    ng = gk.shape[0]
+    kx, ky, kz = _kgrid(ng, box_size, gk.device)
+    k2 = kx * kx + ky * ky + kz * kz
+    k2[0, 0, 0] = 1.0
+    ka = (kx, ky, kz)[axis]
+    fac = (ka / k2).to(torch.float32)
+    psi_k = gk * (1j * fac)
+    psi_k[0, 0, 0] = 0.0
+    return torch.fft.irfftn(psi_k, s=(ng, ng, ng))
+
+
+def lognormal_catalog(n: int, box_size: float, ngrid: int, seed: int, slope: float = -1.5,
+                      variance: float = 1.0, f_rsd: float = 0.75, device="cpu",
+                      dtype=torch.float32):
+    """n objects Poisson-sampled from a log-normal field on an ngrid^3 grid.
+
+    1 + delta = exp(G - sigma_G^2 / 2) with G Gaussian, P_G(k) = A k^slope and A
+    chosen so sigma_G^2 = `variance` at the cell scale.  Exactly n objects are
+    drawn by inverse-CDF sampling of cells with probability proportional to
+    1 + delta (a multinomial draw), placed uniformly inside their cell, then
+    displaced along z by f_rsd * psi_z with psi the linear displacement of G
+    (redshift-space distortion), and wrapped into [0, L).  Shape (n, 3)."""
+    gk, _ = gaussian_field_k(ngrid, box_size, slope, seed, device, variance=variance)
+    g = torch.fft.irfftn(gk, s=(ngrid, ngrid, ngrid))
+    sig2 = float(g.double().var())
+    rho = torch.exp(g.double() - 0.5 * sig2).reshape(-1)
+    del g
+    cdf = torch.cumsum(rho, 0)
+    del rho
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) + 1)
+    u = torch.rand(n, generator=gen, device=device, dtype=torch.float64) * float(cdf[-1])
+    cell = torch.searchsorted(cdf, u).clamp_(max=ngrid ** 3 - 1)
+    del cdf, u
+    H = box_size / ngrid
+    ix = cell // (ngrid * ngrid)
+    iy = (cell // ngrid) % ngrid
+    iz = cell % ngrid
+    off = torch.rand((n, 3), generator=gen, device=device, dtype=torch.float64)
+    pos = torch.stack([ix, iy, iz], dim=1).to(torch.float64).add_(off).mul_(H)
+    del off
+    if f_rsd:
+        psi_z = _displacement(gk, box_size, 2).reshape(-1)
+        pos[:, 2] += f_rsd * psi_z[cell].to(torch.float64)
+        del psi_z
+        pos[:, 2] = torch.remainder(pos[:, 2], box_size)
+    return pos.to(dtype)
+
+
+def zeldovich_lattice(nside: int, box_size: float, seed: int, slope: float = -2.0,
+                      rms_frac: float = 0.25, device="cpu", dtype=torch.float32):
+    """nside^3 objects on a lattice (spacing L / nside) displaced by the linear
+    (Zel'dovich) displacement of a Gaussian field with P(k) ~ k^slope, scaled
+    so the rms displacement is rms_frac lattice spacings; wrapped into [0, L).
+    Shape (nside^3, 3)."""
+    gk, _ = gaussian_field_k(nside, box_size, slope, seed, device, variance=1.0)
+    spacing = box_size / nside
+    psis = [_displacement(gk, box_size, a) for a in range(3)]
+    rms = math.sqrt(sum(float((p.double() ** 2).mean()) for p in psis))
+    scale = rms_frac * spacing / rms
+    del gk
+    out = torch.empty((nside ** 3, 3), device=device, dtype=dtype)
+    q = torch.arange(nside, device=device, dtype=torch.float64) * spacing
+    for a in range(3):
+        shape = [1, 1, 1]
+        shape[a] = nside
+        qa = q.reshape(shape).expand(nside, nside, nside)
+        x = torch.remainder(qa + scale * psis[a].double(), box_size)
+        out[:, a] = x.reshape(-1).to(dtype)
+        psis[a] = None
+        del x
+    return out

@@ -1,0 +1,81 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+declared in include/pk.h, and rejects bad arguments with PK_EINVAL before any
+CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pk():
+    import paper_1712_05834_gb300 as pk
+    pk.build()
+    pk.load()
+    return pk
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "pk.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pk_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_function(pk):
+    names = header_functions()
+    assert "pk_plan" in names and "pk_compute" in names and len(names) >= 10
+    lib = ctypes.CDLL(pk.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(names) <= set(pk.EXPORTED)
+
+
+def test_config_default(pk):
+    c = pk.pk_config_default()
+    assert c.box_size == 1000.0 and c.nmesh == 256 and c.window == pk.PK_CIC
+    assert c.compensated == 1 and c.interlaced == 0 and c.los_axis == 2
+    assert c.poles_mask == 7 and c.batch == 1 and c.subtract_shot == 1
+    assert abs(c.dk - 2 * 2 * 3.141592653589793 / 1000.0) < 1e-15
+
+
+def test_status_strings(pk):
+    for s in range(8):
+        assert pk.pk_status_string(s).startswith("PK_")
+    assert "unknown" in pk.pk_status_string(99)
+
+
+@pytest.mark.parametrize("field,value,word", [
+    ("nmesh", 63, "nmesh"), ("nmesh", 2, "nmesh"), ("nmesh", 8192, "nmesh"),
+    ("box_size", 0.0, "box_size"), ("box_size", -1.0, "box_size"),
+    ("window", 5, "window"), ("dk", 0.0, "dk"), ("kmin", -0.1, "kmin"),
+    ("nmu", -1, "nmu"), ("los_axis", 0, "los_axis"), ("precision", 3, "precision"),
+    ("fixed_scale_log2", 50, "fixed_scale_log2"), ("batch", -2, "batch"),
+    ("poles_mask", 8, "poles_mask"),
+])
+def test_plan_rejects_bad_config(pk, field, value, word):
+    c = pk.make_config(1000.0, 64, "cic", dk=0.01)
+    setattr(c, field, value)
+    with pytest.raises(pk.PkError) as e:
+        pk.pk_plan(c)
+    assert e.value.status == pk.PK_EINVAL
+    assert word in str(e.value)
+
+
+def test_plan_rejects_empty_binning(pk):
+    c = pk.make_config(1000.0, 64, "cic", dk=10.0)
+    with pytest.raises(pk.PkError) as e:
+        pk.pk_plan(c)
+    assert e.value.status == pk.PK_EINVAL
+
+
+def test_null_arguments(pk):
+    lib = pk.load()
+    c = pk.make_config(1000.0, 64, "cic", dk=0.01)
+    assert lib.pk_plan(ctypes.byref(c), None, None) == pk.PK_EINVAL
+    assert lib.pk_paint(None, None, 0, None, 0, 0) == pk.PK_EINVAL
+    assert lib.pk_compute(None) == pk.PK_EINVAL
+    assert lib.pk_destroy(None) == pk.PK_OK
+    assert lib.pk_last_error(None) == b""
