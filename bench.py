@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="timed steps only (no e2e leg, no CPU baseline, no clock sampler): for ncu")
     return ap.parse_args()
 
 
@@ -173,6 +175,24 @@ def oracle_sample_text():
             (ORACLE_PAINT_FRACTION, ORACLE_PAINT_FRACTION))
 
 
+def binned_stored_modes():
+    """Stored half-grid modes that fall in a k bin (0 < |k|, kmin <= k < kmax):
+    the modes the bin pass must read.  Same FP64 bin rule as the library."""
+    import numpy as np
+    N = NMESH
+    kF = (2.0 * math.pi) / L_BOX
+    nk = int(math.floor(((math.pi * N) / L_BOX) / DK))
+    f = np.where(np.arange(N) < N // 2, np.arange(N), np.arange(N) - N)
+    r2 = (f[:, None] ** 2 + f[None, :] ** 2).reshape(-1)
+    l2 = np.arange(N // 2 + 1) ** 2
+    total = 0
+    for chunk in np.array_split(r2, 64):
+        m = chunk[:, None] + l2[None, :]
+        b = np.floor((kF * np.sqrt(m.astype(np.float64)) - 0.0) / DK)
+        total += int(np.count_nonzero((m > 0) & (b >= 0) & (b < nk)))
+    return total
+
+
 def make_catalog(rank, device):
     import synth
     return synth.lognormal_catalog(NPART, L_BOX, NMESH, synth.seed_for(2, rank), device=device)
@@ -238,11 +258,12 @@ def main():
     stream = torch.cuda.Stream()
     pos = make_catalog(rank, "cuda")
     torch.cuda.synchronize()
+    torch.cuda.empty_cache()                     # drop the generator's temporaries
     cfg = pk.make_config(L_BOX, NMESH, "tsc", interlaced=True, dk=DK, nmu=NMU, precision="f32")
     with torch.cuda.stream(stream):
         plan = pk.pk_plan(cfg, stream)
         pk.pk_enable_timing(plan, True)
-        flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+        flush = torch.empty((1 if args.profile else 512) * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
         def step():
             pk.pk_paint(plan, pos)
@@ -257,9 +278,10 @@ def main():
             uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
         except Exception:
             pass
-        clocks = ClockSampler(uuid)
-        clocks.start()
-        time.sleep(0.3)
+        clocks = ClockSampler(None if args.profile else uuid)
+        if not args.profile:
+            clocks.start()
+            time.sleep(0.3)
         barrier(world)
         torch.cuda.synchronize()
         launches0 = pk.pk_launch_count(plan)
@@ -284,17 +306,19 @@ def main():
         total_s = max_over_ranks(sum(step_ms) / 1e3, world)
 
         # e2e through the public API with host (pinned) buffers
-        host = pos.cpu().pin_memory()
-        e2e_steps = max(3, min(args.steps, 20))
-        torch.cuda.synchronize()
-        barrier(world)
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            pk.pk_paint(plan, host)
-            pk.pk_compute(plan)
-            res_e2e = pk.pk_result(plan, 0)
-        torch.cuda.synchronize()
-        e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+        e2e_steps, e2e_s = 0, float("nan")
+        if not args.profile:
+            host = pos.cpu().pin_memory()
+            e2e_steps = max(3, min(args.steps, 20))
+            torch.cuda.synchronize()
+            barrier(world)
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                pk.pk_paint(plan, host)
+                pk.pk_compute(plan)
+                pk.pk_result(plan, 0)
+            torch.cuda.synchronize()
+            e2e_s = max_over_ranks(time.perf_counter() - t0, world)
         pk.pk_destroy(plan)
 
     if rank != 0:
@@ -303,10 +327,11 @@ def main():
     value = world * K / total_s
     med = {s: statistics.median(v) for s, v in stages.items()}
     nmodes = NMESH * NMESH * (NMESH // 2 + 1)
+    nbinned = binned_stored_modes()
     hbm, peak_kind = peaks()
     # algorithmic bytes per launch
     paint_bytes = NPART * 12 + 2 * NMESH ** 3 * 4            # xyz FP32 in + 2 FP32 meshes out
-    bin_bytes = 2 * nmodes * 8                               # 2 complex64 meshes read
+    bin_bytes = 2 * nbinned * 8                              # the binned modes of 2 complex64 meshes
     roof = {
         "paint": {"bound": "hbm", "achieved": paint_bytes / (med["sort"] + med["paint"]) / 1e6,
                   "stage_ms": med["sort"] + med["paint"], "bytes": paint_bytes,
@@ -334,7 +359,8 @@ def main():
                    "parallelism": "replicas" if world == 1 else "dp%d (independent catalogs)" % world},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
         "particles_painted_per_s": NPART / ((med["sort"] + med["paint"]) / 1e3),
-        "modes_binned_per_s": 2 * nmodes / (med["bin"] / 1e3),
+        "modes_binned_per_s": nbinned / (med["bin"] / 1e3),
+        "stored_modes": nmodes, "binned_stored_modes": nbinned,
         "stage_ms_median": med,
         "fft_ms": med["fft"],
         "roofline": rl,
@@ -345,7 +371,7 @@ def main():
                 "h2d_bytes_per_step": int(NPART * 12), "d2h_bytes_per_step": int(res_bytes)},
         "wall_s_timed": wall,
     }
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and not args.profile:
         import oracle
         oracle.build()
         pos64 = pos.double().cpu().numpy()

@@ -87,7 +87,8 @@ typedef struct {
     int los_axis;           /* must be 2 (z)                                     */
     int precision;          /* pk_precision                                      */
     int subtract_shot;      /* 0 / 1                                             */
-    int fixed_scale_log2;   /* S: one weight unit = 2^S; 0 selects 32; 1..40     */
+    int fixed_scale_log2;   /* S: one weight unit = 2^S; 0 selects 22 (FP32 mesh)
+                               or 32 (FP64 mesh); 1..40                          */
     int batch;              /* catalogs per plan (separate meshes); 0 -> 1       */
     int tile;               /* paint tile edge in cells; 0 -> automatic          */
 } pk_config;
@@ -114,7 +115,7 @@ typedef struct {
 
 /* Fill *cfg with defaults: L = 1000, N = 256, CIC, not interlaced, compensated,
  * kmin = 0, kmax = k_N, dk = 2 kF, nmu = 0, all poles, z line of sight, FP32
- * mesh, shot noise subtracted, S = 32, batch 1, automatic tile. */
+ * mesh, shot noise subtracted, S automatic, batch 1, automatic tile. */
 void pk_config_default(pk_config *cfg);
 
 /* Create a plan: validates cfg, allocates the meshes (in-place r2c layout,

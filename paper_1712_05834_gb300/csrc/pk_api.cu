@@ -45,21 +45,25 @@ struct pk_plan_s {
     cufftHandle fft = 0;
     bool fft_made = false;
 
-    uint32_t *d_count = nullptr;
-    int64_t *d_off = nullptr, *d_scan_tmp = nullptr;
-    float4 *d_sorted = nullptr;
+    uint32_t *d_count = nullptr;     // objects per (tile, class) key
+    uint32_t *d_off = nullptr;       // exclusive scan of d_count (+ total)
+    uint32_t *d_scan_tmp = nullptr;
+    uint32_t *d_rank = nullptr;      // rank of each object inside its key
+    float4 *d_sorted = nullptr;      // objects in key order, home-tile-local xyz + w
     int64_t sorted_cap = 0;
+    long long nkeys = 0;             // keys per catalog
     void *d_stage = nullptr;
     size_t stage_cap = 0;
-    int64_t *d_item_off = nullptr, *h_item_off = nullptr, *h_total = nullptr;
-    double *d_wsums = nullptr;
+    int64_t *d_item_off = nullptr, *h_item_off = nullptr;
+    double *d_wsums = nullptr;       // per catalog: sum w, sum w^2, sum |w|, spare
+    unsigned *d_wmax = nullptr;      // per catalog: max |w| as float bits
     int *d_err = nullptr;           // bit 1: tile sort inconsistency (never expected)
 
     void *d_cw = nullptr, *d_ph = nullptr;
     int *d_kedge = nullptr;
     int G_total = 0;
     void *d_partial = nullptr;
-    double *d_sums = nullptr, *d_res = nullptr, *h_res = nullptr;
+    double *d_sums2 = nullptr, *d_res = nullptr, *h_res = nullptr;
     unsigned long long *d_modes1d = nullptr, *d_modes2d = nullptr;
 
     std::vector<int> kedge;
@@ -114,12 +118,13 @@ void free_plan(pk_plan_s *p) {
     if (!p) return;
     cudaStreamSynchronize(p->st);
     if (p->fft_made) cufftDestroy(p->fft);
-    void *dev[] = {p->mesh, p->d_count, p->d_off, p->d_scan_tmp, p->d_sorted, p->d_stage,
-                   p->d_item_off, p->d_wsums, p->d_cw, p->d_ph, p->d_kedge, p->d_partial,
-                   p->d_sums, p->d_res, p->d_modes1d, p->d_modes2d, p->d_err};
+    void *dev[] = {p->mesh, p->d_count, p->d_off, p->d_scan_tmp, p->d_rank, p->d_sorted,
+                   p->d_stage, p->d_item_off, p->d_wsums, p->d_wmax, p->d_cw, p->d_ph,
+                   p->d_kedge, p->d_partial, p->d_sums2, p->d_res, p->d_modes1d, p->d_modes2d,
+                   p->d_err};
     for (void *d : dev)
         if (d) cudaFree(d);
-    void *host[] = {p->h_item_off, p->h_total, p->h_res};
+    void *host[] = {p->h_item_off, p->h_res};
     for (void *h : host)
         if (h) cudaFreeHost(h);
     if (p->done) cudaEventDestroy(p->done);
@@ -147,19 +152,19 @@ void window_reach(int p, int interlaced, int *lo, int *hi) {
     }
 }
 
-int choose_tile(int N, int nm, int requested) {
-    const size_t kMaxSmem = 200 * 1024;
-    auto fits = [&](int T) { return paint_smem_bytes(T, nm) <= kMaxSmem; };
-    if (requested > 0) return (N % requested == 0 && fits(requested)) ? requested : -1;
-    int best = 0;
-    for (int T = 1; T <= 16 && T <= N; ++T)
-        if (N % T == 0) best = T;
+// Tile edge: a divisor of N with T >= hi - lo (so an object's window reaches at
+// most one neighbour per axis) and 2 T^3 uint32 of shared memory.  Prefers the
+// largest divisor <= 16, else the smallest in [17, 28].
+int choose_tile(int N, int span, int requested) {
+    const int tmin = span > 1 ? span : 1;
+    auto ok = [&](int T) { return T >= tmin && N % T == 0 && paint_smem_bytes(T) <= 200 * 1024; };
+    if (requested > 0) return ok(requested) ? requested : -1;
+    int best = -1;
+    for (int T = tmin; T <= 16 && T <= N; ++T)
+        if (ok(T)) best = T;
     if (best < 8) {
-        for (int T = 17; T <= 24 && T <= N; ++T)
-            if (N % T == 0 && fits(T)) {
-                best = T;
-                break;
-            }
+        for (int T = 17; T <= 28 && T <= N; ++T)
+            if (ok(T)) return T;
     }
     return best;
 }
@@ -249,11 +254,14 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
     P->B = c.batch > 0 ? c.batch : 1;
     P->f64 = c.precision == PK_MESH_F64;
     P->esz = P->f64 ? 8 : 4;
-    P->S = c.fixed_scale_log2 > 0 ? c.fixed_scale_log2 : 32;
+    P->S = c.fixed_scale_log2 > 0 ? c.fixed_scale_log2 : (P->f64 ? 32 : 22);
     P->mesh_reals = (long long)P->N * P->N * 2 * P->Nh;
 
-    const int T = choose_tile(P->N, P->nm, c.tile);
-    if (T <= 0) return fail(P, PK_EINVAL, "tile must divide nmesh and fit in shared memory");
+    int rlo, rhi;
+    window_reach(P->p, c.interlaced, &rlo, &rhi);
+    const int T = choose_tile(P->N, rhi - rlo, c.tile);
+    if (T <= 0)
+        return fail(P, PK_EINVAL, "tile must divide nmesh, be >= the window reach and fit in shared memory");
     const double L = c.box_size;
     P->kF = (2.0 * M_PI) / L;
     const double kmax = c.kmax > 0.0 ? c.kmax : (M_PI * P->N) / L;
@@ -270,8 +278,10 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
     pg.N = P->N;
     pg.T = T;
     pg.ntx = P->N / T;
-    window_reach(P->p, c.interlaced, &pg.lo, &pg.hi);
+    pg.lo = rlo;
+    pg.hi = rhi;
     pg.ntiles = (long long)pg.ntx * pg.ntx * pg.ntx;
+    P->nkeys = pg.ntiles * paint_classes();
 
     // ---- k bins: exact edges in m space ----
     const long long mcap = 3LL * (P->N / 2) * (P->N / 2) + 1;
@@ -304,6 +314,10 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
     bg.mlo = P->kedge[0];
     bg.mhi = P->kedge[nk];
     bg.modes = (long long)P->N * P->N * P->Nh;
+    bg.inv_Nh = 1.0f / (float)P->Nh;
+    bg.inv_N = 1.0f / (float)P->N;
+    bg.mu32 = (double)(nmu + 1) * (nmu + 1) * (double)(bg.mhi + 1) < 4294967295.0 &&
+              (double)nmu * nmu * (double)(P->N / 2) * (P->N / 2) < 4294967295.0;
     if (bin_smem_bytes(bg, P->f64) > 200 * 1024)
         return fail(P, PK_EINVAL, "too many (k, mu) bins for the per-CTA histogram");
 
@@ -326,24 +340,23 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
     PK_CUDA(P, cudaEventCreateWithFlags(&P->done, cudaEventDisableTiming));
     const size_t mesh_bytes = (size_t)P->B * P->nm * P->mesh_reals * P->esz;
     PK_CUDA(P, dev_alloc(&P->mesh, mesh_bytes));
-    const long long ntiles_all = (long long)P->B * pg.ntiles;
-    PK_CUDA(P, dev_alloc(&P->d_count, sizeof(uint32_t) * ntiles_all));
-    PK_CUDA(P, cudaMemset(P->d_count, 0, sizeof(uint32_t) * ntiles_all));
-    PK_CUDA(P, dev_alloc(&P->d_off, sizeof(int64_t) * (ntiles_all + 1)));
-    PK_CUDA(P, dev_alloc(&P->d_scan_tmp, sizeof(int64_t) * 4096));
+    const long long keys_all = (long long)P->B * P->nkeys;
+    PK_CUDA(P, dev_alloc(&P->d_count, sizeof(uint32_t) * keys_all));
+    PK_CUDA(P, dev_alloc(&P->d_off, sizeof(uint32_t) * (keys_all + 1)));
+    PK_CUDA(P, dev_alloc(&P->d_scan_tmp, sizeof(uint32_t) * scan_tmp_elems(keys_all)));
     PK_CUDA(P, dev_alloc(&P->d_item_off, sizeof(int64_t) * (P->B + 1)));
     PK_CUDA(P, cudaMallocHost(reinterpret_cast<void **>(&P->h_item_off), sizeof(int64_t) * (P->B + 1)));
-    PK_CUDA(P, cudaMallocHost(reinterpret_cast<void **>(&P->h_total), sizeof(int64_t)));
-    PK_CUDA(P, dev_alloc(&P->d_wsums, sizeof(double) * 3 * P->B));
+    PK_CUDA(P, dev_alloc(&P->d_wsums, sizeof(double) * 4 * P->B));
+    PK_CUDA(P, dev_alloc(&P->d_wmax, sizeof(unsigned) * P->B));
     PK_CUDA(P, dev_alloc(&P->d_err, sizeof(int)));
     PK_CUDA(P, cudaMemset(P->d_err, 0, sizeof(int)));
     PK_CUDA(P, dev_alloc(&P->d_cw, P->esz * P->N));
     PK_CUDA(P, dev_alloc(&P->d_ph, 2 * P->esz * (P->N + 1)));
     PK_CUDA(P, dev_alloc(&P->d_kedge, sizeof(int) * (nk + 1)));
-    const int occ = bin_ctas_per_sm(bg, P->f64, c.interlaced);
+    const int occ = bin_ctas_per_sm(bg, P->f64);
     P->G_total = P->nsm * occ;
     PK_CUDA(P, dev_alloc(&P->d_partial, (size_t)(P->G_total + P->B) * bg.nh * (P->f64 ? 8 : 4)));
-    PK_CUDA(P, dev_alloc(&P->d_sums, sizeof(double) * (size_t)P->B * bg.nh));
+    PK_CUDA(P, dev_alloc(&P->d_sums2, sizeof(double) * (size_t)(reduce_chunks(P->G_total) + P->B) * bg.nh));
     PK_CUDA(P, dev_alloc(&P->d_res, sizeof(double) * (size_t)P->B * fg.RL));
     PK_CUDA(P, cudaMallocHost(reinterpret_cast<void **>(&P->h_res), sizeof(double) * (size_t)P->B * fg.RL));
     const int nq = nmu > 0 ? nmu : 1;
@@ -393,8 +406,8 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
         if (e == cudaSuccess) e = cudaMemset(HL, 0, sizeof(unsigned long long) * hn);
         if (e == cudaSuccess) e = launch_geom_hist(bg, H, HL, nullptr);
         if (e == cudaSuccess)
-            e = launch_geom_finalize(bg, P->d_kedge, P->kF, H, HL, nullptr, nullptr, P->d_modes2d,
-                                     kmean2d, mumean2d, nullptr);
+            e = launch_geom_finalize(bg, P->d_kedge, P->kF, H, HL, P->d_modes2d, kmean2d, mumean2d,
+                                     nullptr);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         P->launches += 2;
         P->modes2d.resize((size_t)nk * nq);
@@ -521,35 +534,44 @@ static pk_status paint_impl(pk_plan_s *P, const void *pos, int dtype, const floa
         }
     }
 
-    const long long ntiles = (long long)nitems * P->pg.ntiles;
+    if (ntot >= (int64_t)0xffffffffLL)
+        return fail(P, PK_EINVAL, "at most 2^32 - 2 objects per paint call");
+    if (ntot > P->sorted_cap) {                 // grow the key-ordered copy (rare)
+        PK_CUDA(P, cudaStreamSynchronize(st));
+        if (P->d_sorted) cudaFree(P->d_sorted);
+        if (P->d_rank) cudaFree(P->d_rank);
+        P->d_sorted = nullptr;
+        P->d_rank = nullptr;
+        P->sorted_cap = 0;
+        PK_CUDA(P, cudaMalloc(reinterpret_cast<void **>(&P->d_sorted), sizeof(float4) * (size_t)ntot));
+        PK_CUDA(P, cudaMalloc(reinterpret_cast<void **>(&P->d_rank), sizeof(uint32_t) * (size_t)ntot));
+        P->sorted_cap = ntot;
+    }
+    const long long nkeys = (long long)nitems * P->nkeys;
     if (P->timing) PK_CUDA(P, cudaEventRecord(P->tev[0], st));
     memcpy(P->h_item_off, offsets, sizeof(int64_t) * (nitems + 1));
     PK_CUDA(P, cudaMemcpyAsync(P->d_item_off, P->h_item_off, sizeof(int64_t) * (nitems + 1),
                                cudaMemcpyHostToDevice, st));
-    PK_CUDA(P, cudaMemsetAsync(P->d_count, 0, sizeof(uint32_t) * ntiles, st));
-    if (!accumulate) PK_CUDA(P, cudaMemsetAsync(P->d_wsums, 0, sizeof(double) * 3 * nitems, st));
-    PK_CUDA(P, launch_tile_count(dpos, dtype, dw, P->d_item_off, nitems, max_n, P->pg, P->d_count,
-                                 P->d_wsums, st));
-    PK_CUDA(P, launch_scan(P->d_count, ntiles, P->d_off, P->d_scan_tmp, st));
-    PK_CUDA(P, cudaMemcpyAsync(P->h_total, P->d_off + ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    PK_CUDA(P, cudaStreamSynchronize(st));
-    const int64_t total = *P->h_total;
-    if (total > P->sorted_cap) {
-        if (P->d_sorted) cudaFree(P->d_sorted);
-        P->d_sorted = nullptr;
-        P->sorted_cap = 0;
-        const int64_t cap = total + total / 8 + 1024;
-        PK_CUDA(P, cudaMalloc(reinterpret_cast<void **>(&P->d_sorted), sizeof(float4) * (size_t)cap));
-        P->sorted_cap = cap;
+    PK_CUDA(P, cudaMemsetAsync(P->d_count, 0, sizeof(uint32_t) * nkeys, st));
+    if (!accumulate) {
+        PK_CUDA(P, cudaMemsetAsync(P->d_wsums, 0, sizeof(double) * 4 * nitems, st));
+        PK_CUDA(P, cudaMemsetAsync(P->d_wmax, 0, sizeof(unsigned) * nitems, st));
     }
-    PK_CUDA(P, launch_tile_scatter(dpos, dtype, dw, P->d_item_off, nitems, max_n, P->pg, P->d_count,
-                                   P->d_off, P->d_sorted, P->d_err, st));
+    int launches = 2;   // count, scatter
+    PK_CUDA(P, launch_sort_count(dpos, dtype, dw, P->d_item_off, nitems, max_n, P->pg, P->d_count,
+                                 P->d_rank, P->d_wsums, P->d_wmax, st));
+    PK_CUDA(P, launch_scan(P->d_count, nkeys, P->d_off, P->d_scan_tmp, &launches, st));
+    PK_CUDA(P, launch_sort_scatter(dpos, dtype, dw, P->d_item_off, nitems, max_n, P->pg, P->d_off,
+                                   P->d_rank, P->d_sorted, P->d_err, st));
     if (P->timing) PK_CUDA(P, cudaEventRecord(P->tev[1], st));
+    const int unit_weights = dw == nullptr && dtype != PK_F32X4;
     PK_CUDA(P, launch_paint_tiles(P->d_sorted, P->d_off, nitems, P->pg, P->p, P->nm, P->S, P->f64,
-                                  P->mesh, P->nm * P->mesh_reals, P->mesh_reals, accumulate, st));
+                                  P->d_wmax, unit_weights, P->mesh, P->nm * P->mesh_reals,
+                                  P->mesh_reals, accumulate, st));
+    launches += 1;
     if (P->timing) PK_CUDA(P, cudaEventRecord(P->tev[2], st));
     P->tev_paint = P->timing;
-    P->launches += 6;   // count, 3 scan kernels, scatter, paint
+    P->launches += launches;
     P->npainted = nitems;
     P->transformed = 0;
     return PK_OK;
@@ -594,8 +616,8 @@ pk_status pk_compute(pk_plan_t P) {
     PK_CUDA(P, launch_bin(P->mesh, P->f64, P->cfg.interlaced, item_c, mesh_c, nitems, G, P->bg,
                           P->d_cw, P->d_ph, P->d_kedge, P->d_partial, st));
     if (P->timing) PK_CUDA(P, cudaEventRecord(P->tev[5], st));
-    PK_CUDA(P, launch_bin_reduce(P->d_partial, P->f64, G, P->bg.nh, nitems, P->d_sums, st));
-    PK_CUDA(P, launch_finalize(P->d_sums, P->d_modes1d, P->d_modes2d, P->d_wsums, P->d_err, P->fg,
+    PK_CUDA(P, launch_bin_reduce(P->d_partial, P->f64, G, P->bg.nh, nitems, P->d_sums2, st));
+    PK_CUDA(P, launch_finalize(P->d_sums2, G, P->d_modes1d, P->d_modes2d, P->d_wsums, P->d_err, P->fg,
                                nitems, P->d_res, st));
     if (P->timing) PK_CUDA(P, cudaEventRecord(P->tev[6], st));
     P->tev_compute = P->timing;

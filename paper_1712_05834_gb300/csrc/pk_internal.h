@@ -10,15 +10,15 @@
 namespace pk {
 
 // Geometry of the tile-sorted paint (Sec. 3.3.1 painting, Sec. 3.3.2 windows).
-// The mesh is cut into cubic tiles of T^3 cells; an object is copied into every
-// tile that any of its window nodes (on either interlaced mesh) falls in, with
-// its position stored relative to that tile's origin.  Cells [floor(s)+lo,
-// floor(s)+hi] along each axis cover the support of both meshes.
+// The mesh is cut into cubic tiles of T^3 cells.  Each object is sorted by
+// (home tile, boundary class); the paint CTA of a tile gathers its own objects
+// and the boundary classes of its 26 neighbours.  Cells [floor(s)+lo,
+// floor(s)+hi] along each axis cover the window support on both meshes.
 struct PaintGeom {
     float invH;         // N / L in FP32
     double invHd;       // N / L in FP64
     int N;              // cells per side
-    int T;              // tile edge (divides N)
+    int T;              // tile edge (divides N, T >= hi - lo)
     int ntx;            // tiles per side = N / T
     int lo, hi;         // reach of the window support relative to floor(s)
     long long ntiles;   // ntx^3 tiles per catalog
@@ -34,6 +34,8 @@ struct BinGeom {
     float kscale, koff;     // bin estimate: sqrt(m) * kscale - koff
     int mlo, mhi;           // binned modes have mlo <= m < mhi (and m != 0)
     long long modes;        // stored modes per mesh: N * N * Nh
+    float inv_Nh, inv_N;    // 1 / Nh, 1 / N (quotient estimates, corrected exactly)
+    int mu32;               // nmu^2 * max m < 2^32: mu-bin checks in 32 bits
 };
 
 struct FinalGeom {
@@ -52,32 +54,34 @@ struct ResultLayout {
 ResultLayout result_layout(int nk, int nmu);
 
 // ---- launchers (pk_kernels.cu); all asynchronous on `st` ----
-cudaError_t launch_tile_count(const void *pos, int dtype, const float *w, const int64_t *item_off,
+int paint_classes();                  // boundary classes per tile (27)
+size_t paint_smem_bytes(int T);
+size_t scan_tmp_elems(int64_t n);
+cudaError_t launch_sort_count(const void *pos, int dtype, const float *w, const int64_t *item_off,
                               int nitems, int64_t max_n, const PaintGeom &g, uint32_t *count,
-                              double *wsums, cudaStream_t st);
-cudaError_t launch_scan(const uint32_t *count, int64_t n, int64_t *off, int64_t *block_tmp,
+                              uint32_t *rank, double *wsums, unsigned *wmax, cudaStream_t st);
+cudaError_t launch_scan(const uint32_t *in, int64_t n, uint32_t *out, uint32_t *tmp, int *launches,
                         cudaStream_t st);
-cudaError_t launch_tile_scatter(const void *pos, int dtype, const float *w,
-                                const int64_t *item_off, int nitems, int64_t max_n,
-                                const PaintGeom &g, uint32_t *count, const int64_t *off,
-                                float4 *sorted, int *err, cudaStream_t st);
-cudaError_t launch_paint_tiles(const float4 *sorted, const int64_t *off, int nitems,
+cudaError_t launch_sort_scatter(const void *pos, int dtype, const float *w, const int64_t *item_off,
+                                int nitems, int64_t max_n, const PaintGeom &g, const uint32_t *off,
+                                const uint32_t *rank, float4 *sorted, int *err, cudaStream_t st);
+cudaError_t launch_paint_tiles(const float4 *sorted, const uint32_t *off, int nitems,
                                const PaintGeom &g, int window, int nmesh, int S, int f64,
-                               void *mesh, long long item_stride, long long mesh_stride,
-                               int accumulate, cudaStream_t st);
-size_t paint_smem_bytes(int T, int nmesh);
+                               const unsigned *wmax, int unit_weights, void *mesh,
+                               long long item_stride, long long mesh_stride, int accumulate,
+                               cudaStream_t st);
 
 cudaError_t launch_bin(const void *mesh, int f64, int interlaced, long long item_stride_c,
                        long long mesh_stride_c, int nitems, int ctas_per_item,
                        const BinGeom &g, const void *cw, const void *ph, const int *kedge,
                        void *partial, cudaStream_t st);
 size_t bin_smem_bytes(const BinGeom &g, int f64);
-int bin_ctas_per_sm(const BinGeom &g, int f64, int interlaced);
+int bin_ctas_per_sm(const BinGeom &g, int f64);
 int bin_threads();
-
+int reduce_chunks(int G);
 cudaError_t launch_bin_reduce(const void *partial, int f64, int G, int nh, int nitems,
-                              double *sums, cudaStream_t st);
-cudaError_t launch_finalize(const double *sums, const unsigned long long *modes1d,
+                              double *sums2, cudaStream_t st);
+cudaError_t launch_finalize(const double *sums2, int G, const unsigned long long *modes1d,
                             const unsigned long long *modes2d, const double *wsums, const int *err,
                             const FinalGeom &f, int nitems, double *res, cudaStream_t st);
 
@@ -85,8 +89,7 @@ cudaError_t launch_geom_hist(const BinGeom &g, unsigned long long *H, unsigned l
                              cudaStream_t st);
 cudaError_t launch_geom_finalize(const BinGeom &g, const int *kedge, double kF,
                                  const unsigned long long *H, const unsigned long long *HL,
-                                 unsigned long long *modes1d, double *kmean1d,
-                                 unsigned long long *modes2d, double *kmean2d,
-                                 double *mumean2d, cudaStream_t st);
+                                 unsigned long long *modes2d, double *kmean2d, double *mumean2d,
+                                 cudaStream_t st);
 
 }  // namespace pk

@@ -1,25 +1,37 @@
 // pk_kernels.cu -- sm_103a kernels of the FFT power-spectrum path.
 //
-//   k_tile_count    pass 1 of the tile counting sort: wrap each object into the
-//                   box, find the tiles its window support touches (on both
-//                   interlaced meshes), count copies per tile; sum w, w^2, |w|.
-//   k_scan_*        exclusive scan of the tile counts (int64 offsets).
-//   k_tile_scatter  pass 2: write one float4 (tile-local x, y, z, w) per copy.
-//   k_paint_tiles   one CTA per tile: accumulate the window deposits of every
-//                   copy in shared memory as int64 fixed point (order-free, so
-//                   the mesh is bit-identical run to run), then write the tile
-//                   once, coalesced, into the in-place r2c layout.  No global
-//                   atomics, no global int64 mesh, no separate convert pass.
-//                   Windows: B-splines of order p = 2, 3, 4 (CIC, TSC, PCS),
-//                   Sec. 3.3.2; interlacing: second mesh at x + H/2, Sec. 3.3.2.
-//   k_bin           fused window compensation (Eq. window-deconvolution),
-//                   interlacing combine, |delta|^2, k bin (exact integer edges
-//                   in m = |n|^2), mu bin (exact integer rule), Legendre
-//                   weights; per-CTA shared-memory histograms, Sec. 3.4.1.
-//   k_bin_reduce    fixed-order FP64 sum of the per-CTA histograms.
+// Paint (Sec. 3.3.1 painting; Sec. 3.3.2 CIC / TSC / PCS B-spline windows and
+// interlacing with a second mesh shifted by half a cell):
+//   k_sort_count    wrap each object into the box, find its home tile (T^3
+//                   cells) and its boundary class (per axis: near the low
+//                   face, interior, near the high face -- 27 classes), count
+//                   objects per (tile, class) key and record each object's
+//                   rank inside its key; sum w, w^2, |w| and max |w|.
+//   k_scan_*        exclusive scan of the key counts (uint32).
+//   k_sort_scatter  write one float4 (home-tile-local x, y, z, w) per object
+//                   at offset[key] + rank: no atomics, no copies, size n.
+//   k_paint_tiles   one CTA per tile: gather the tile's own objects and the
+//                   boundary classes of its 26 neighbours whose window reaches
+//                   into it, deposit B-spline weights into shared memory as
+//                   exact int64 fixed point held in two uint32 words per cell
+//                   (the split point is chosen per tile so the low word can
+//                   never carry; shared 32-bit atomics are ~5x faster than
+//                   64-bit ones here), then write the tile once, coalesced,
+//                   into the in-place r2c layout.  One mesh per pass; the
+//                   interlaced mesh is a second pass over the same objects.
+//                   Integer adds are order-free: the mesh is bit-identical
+//                   run to run and for any object order.
+// Bin (Sec. 3.4.1, Eq. window-deconvolution):
+//   k_bin           per stored mode: interlace combine, sinc^p compensation,
+//                   |delta|^2, k bin (exact integer edges in m = |n|^2), mu
+//                   bin (exact integer rule), Legendre mu^2 / mu^4 weights;
+//                   runs of equal bins merged in registers, then per-CTA
+//                   shared-memory histograms.
+//   k_bin_reduce    fixed-order FP64 sums of the per-CTA histograms, in chunks.
 //   k_finalize      normalization L^3 / (sum w)^2, shot noise, multipoles.
-//   k_geom_*        plan-time, geometry-only: exact mode counts per bin and
-//                   mean k, mean mu (integer histograms over m, FP64 sums).
+// Plan time (geometry only):
+//   k_geom_*        exact mode counts per bin and mean k, mean mu from integer
+//                   histograms over (m, mu bin), summed in FP64.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -33,14 +45,14 @@ namespace {
 constexpr int kCountThreads = 256;
 constexpr int kPaintThreads = 256;
 constexpr int kBinThreads = 256;
-constexpr int kBinVec = 4;            // consecutive modes per thread
+constexpr int kBinVec = 8;            // consecutive modes per thread
 constexpr int kScanThreads = 1024;
 constexpr int kScanPer = 4;           // elements per thread in a scan block
 constexpr int kScanTile = kScanThreads * kScanPer;
-
-__device__ __forceinline__ int floordiv(int a, int b) {   // b > 0
-    return a >= 0 ? a / b : -((-a + b - 1) / b);
-}
+constexpr int kClasses = 27;          // boundary classes per tile
+constexpr int kSegments = 75;         // (neighbour, class range) segments per tile
+constexpr int kReduceChunk = 32;      // per-CTA histograms summed per reduce block
+constexpr int kStage = 512;           // candidates staged in shared memory per batch
 
 __device__ __forceinline__ int wrapmod(int a, int n) {
     int r = a % n;
@@ -53,21 +65,26 @@ __device__ __forceinline__ int wrapmod(int a, int n) {
 __device__ __forceinline__ float wrap_cells(float x, float invH, int N) {
     const float n = (float)N;
     float s = __fmul_rn(x, invH);
-    s = __fsub_rn(s, __fmul_rn(n, floorf(__fdiv_rn(s, n))));
-    if (s < 0.0f) s = __fadd_rn(s, n);
-    if (s >= n) s = __fsub_rn(s, n);
+    if (!(s >= 0.0f && s < n)) {
+        s = __fsub_rn(s, __fmul_rn(n, floorf(__fdiv_rn(s, n))));
+        if (s < 0.0f) s = __fadd_rn(s, n);
+        if (s >= n) s = __fsub_rn(s, n);
+        if (!(s >= 0.0f && s < n)) s = 0.0f;            // NaN / inf positions
+    }
     return s;
 }
 __device__ __forceinline__ double wrap_cells(double x, double invH, int N) {
     const double n = (double)N;
     double s = __dmul_rn(x, invH);
-    s = __dsub_rn(s, __dmul_rn(n, floor(__ddiv_rn(s, n))));
-    if (s < 0.0) s = __dadd_rn(s, n);
-    if (s >= n) s = __dsub_rn(s, n);
+    if (!(s >= 0.0 && s < n)) {
+        s = __dsub_rn(s, __dmul_rn(n, floor(__ddiv_rn(s, n))));
+        if (s < 0.0) s = __dadd_rn(s, n);
+        if (s >= n) s = __dsub_rn(s, n);
+        if (!(s >= 0.0 && s < n)) s = 0.0;
+    }
     return s;
 }
 
-// One object: cell-unit coordinates in [0, N) and its weight.
 template <typename R>
 struct Obj {
     R s[3];
@@ -106,12 +123,21 @@ __device__ __forceinline__ Obj<typename PosReal<DT>::type> load_obj(const void *
     return o;
 }
 
-// Unwrapped tile indices u0 .. u0 + nu - 1 that cells floor(s)+lo .. floor(s)+hi hit.
+// Home tile and boundary class of one object.  Along each axis the class is
+// 0 if the window reaches the tile below (c + lo < 0), 2 if it reaches the
+// tile above (c + hi >= T), else 1; T >= hi - lo keeps these disjoint.
 template <typename R>
-__device__ __forceinline__ void tile_span(R s, const PaintGeom &g, int &u0, int &nu) {
-    const int c = (int)floor(s);
-    u0 = floordiv(c + g.lo, g.T);
-    nu = floordiv(c + g.hi, g.T) - u0 + 1;
+__device__ __forceinline__ void home_key(const Obj<R> &o, const PaintGeom &g, int *tile3, int *cls) {
+    int c = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int cell = min((int)floor(o.s[a]), g.N - 1);
+        const int t = cell / g.T;
+        const int cl = cell - t * g.T;
+        tile3[a] = t;
+        c = c * 3 + (cl < -g.lo ? 0 : (cl >= g.T - g.hi ? 2 : 1));
+    }
+    *cls = c;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -120,176 +146,156 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-template <int DT>
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// wsums[4 * item + {0,1,2}] = sum w, sum w^2, sum |w|; wmax[item] = max |w| (float bits).
+template <int DT, bool WEIGHTED>
 __global__ void __launch_bounds__(kCountThreads)
-k_tile_count(const void *__restrict__ pos, const float *__restrict__ w,
+k_sort_count(const void *__restrict__ pos, const float *__restrict__ w,
              const int64_t *__restrict__ item_off, PaintGeom g, uint32_t *__restrict__ count,
-             double *__restrict__ wsums) {
+             uint32_t *__restrict__ rank, double *__restrict__ wsums, unsigned *__restrict__ wmax) {
     using R = typename PosReal<DT>::type;
     const int item = blockIdx.y;
     const int64_t beg = item_off[item], end = item_off[item + 1];
-    uint32_t *cnt = count + (int64_t)item * g.ntiles;
+    const int64_t kbase = (int64_t)item * g.ntiles * kClasses;
     double sw = 0.0, sw2 = 0.0, swa = 0.0;
+    float mw = 0.0f;
     for (int64_t i = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end;
          i += (int64_t)gridDim.x * blockDim.x) {
         const Obj<R> o = load_obj<DT>(pos, w, i, g);
-        int u0[3], nu[3];
-        tile_span<R>(o.s[0], g, u0[0], nu[0]);
-        tile_span<R>(o.s[1], g, u0[1], nu[1]);
-        tile_span<R>(o.s[2], g, u0[2], nu[2]);
-        for (int a = 0; a < nu[0]; ++a) {
-            const int tx = wrapmod(u0[0] + a, g.ntx);
-            for (int b = 0; b < nu[1]; ++b) {
-                const int ty = wrapmod(u0[1] + b, g.ntx);
-                for (int c = 0; c < nu[2]; ++c) {
-                    const int tz = wrapmod(u0[2] + c, g.ntx);
-                    atomicAdd(cnt + ((int64_t)tx * g.ntx + ty) * g.ntx + tz, 1u);
-                }
-            }
+        int t3[3], cls;
+        home_key<R>(o, g, t3, &cls);
+        const int64_t key = kbase + (((int64_t)t3[0] * g.ntx + t3[1]) * g.ntx + t3[2]) * kClasses + cls;
+        rank[i] = atomicAdd(count + key, 1u);
+        if (WEIGHTED) {
+            const double wd = (double)o.w;
+            sw += wd;
+            sw2 += wd * wd;
+            swa += fabs(wd);
+            mw = fmaxf(mw, fabsf(o.w));
         }
-        const double wd = (double)o.w;
-        sw += wd;
-        sw2 += wd * wd;
-        swa += fabs(wd);
     }
-    __shared__ double red[3][kCountThreads / 32];
-    sw = warp_sum(sw);
-    sw2 = warp_sum(sw2);
-    swa = warp_sum(swa);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-        red[0][wid] = sw;
-        red[1][wid] = sw2;
-        red[2][wid] = swa;
-    }
-    __syncthreads();
-    if (threadIdx.x < 3) {
-        double t = 0.0;
-        for (int k = 0; k < kCountThreads / 32; ++k) t += red[threadIdx.x][k];
-        if (t != 0.0) atomicAdd(wsums + 3 * item + threadIdx.x, t);
+    if (WEIGHTED) {
+        __shared__ double red[3][kCountThreads / 32];
+        __shared__ float redm[kCountThreads / 32];
+        sw = warp_sum(sw);
+        sw2 = warp_sum(sw2);
+        swa = warp_sum(swa);
+        mw = warp_max(mw);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) {
+            red[0][wid] = sw;
+            red[1][wid] = sw2;
+            red[2][wid] = swa;
+            redm[wid] = mw;
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            double t = 0.0;
+            for (int k = 0; k < kCountThreads / 32; ++k) t += red[threadIdx.x][k];
+            if (t != 0.0) atomicAdd(wsums + 4 * item + threadIdx.x, t);
+        } else if (threadIdx.x == 3) {
+            float m = 0.0f;
+            for (int k = 0; k < kCountThreads / 32; ++k) m = fmaxf(m, redm[k]);
+            atomicMax(wmax + item, __float_as_uint(m));
+        }
+    } else if (blockIdx.x == 0 && threadIdx.x < 3) {
+        atomicAdd(wsums + 4 * item + threadIdx.x, (double)(end - beg));   // exact below 2^53
+        if (threadIdx.x == 0) atomicMax(wmax + item, __float_as_uint(1.0f));
     }
 }
 
 template <int DT>
 __global__ void __launch_bounds__(kCountThreads)
-k_tile_scatter(const void *__restrict__ pos, const float *__restrict__ w,
-               const int64_t *__restrict__ item_off, PaintGeom g, uint32_t *__restrict__ count,
-               const int64_t *__restrict__ off, float4 *__restrict__ sorted, int *__restrict__ err) {
+k_sort_scatter(const void *__restrict__ pos, const float *__restrict__ w,
+               const int64_t *__restrict__ item_off, PaintGeom g, const uint32_t *__restrict__ off,
+               const uint32_t *__restrict__ rank, float4 *__restrict__ sorted, int *__restrict__ err) {
     using R = typename PosReal<DT>::type;
     const int item = blockIdx.y;
     const int64_t beg = item_off[item], end = item_off[item + 1];
-    const int64_t tbase = (int64_t)item * g.ntiles;
+    const int64_t kbase = (int64_t)item * g.ntiles * kClasses;
     for (int64_t i = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end;
          i += (int64_t)gridDim.x * blockDim.x) {
         const Obj<R> o = load_obj<DT>(pos, w, i, g);
-        int u0[3], nu[3];
-        tile_span<R>(o.s[0], g, u0[0], nu[0]);
-        tile_span<R>(o.s[1], g, u0[1], nu[1]);
-        tile_span<R>(o.s[2], g, u0[2], nu[2]);
-        for (int a = 0; a < nu[0]; ++a) {
-            const int ux = u0[0] + a, tx = wrapmod(ux, g.ntx);
-            const float lx = (float)(o.s[0] - (R)(ux * g.T));
-            for (int b = 0; b < nu[1]; ++b) {
-                const int uy = u0[1] + b, ty = wrapmod(uy, g.ntx);
-                const float ly = (float)(o.s[1] - (R)(uy * g.T));
-                for (int c = 0; c < nu[2]; ++c) {
-                    const int uz = u0[2] + c, tz = wrapmod(uz, g.ntx);
-                    const float lz = (float)(o.s[2] - (R)(uz * g.T));
-                    const int64_t t = tbase + ((int64_t)tx * g.ntx + ty) * g.ntx + tz;
-                    const uint32_t left = atomicSub(count + t, 1u);
-                    if (left == 0u) {              // more copies than counted: never write
-                        atomicOr(err, 2);
-                        continue;
-                    }
-                    sorted[off[t] + (left - 1u)] = make_float4(lx, ly, lz, o.w);
-                }
-            }
+        int t3[3], cls;
+        home_key<R>(o, g, t3, &cls);
+        const int64_t key = kbase + (((int64_t)t3[0] * g.ntx + t3[1]) * g.ntx + t3[2]) * kClasses + cls;
+        const uint32_t dst = off[key] + rank[i];
+        if (dst >= off[key + 1]) {              // count and scatter disagree: never write
+            atomicOr(err, 2);
+            continue;
         }
+        sorted[dst] = make_float4((float)(o.s[0] - (R)(t3[0] * g.T)), (float)(o.s[1] - (R)(t3[1] * g.T)),
+                                  (float)(o.s[2] - (R)(t3[2] * g.T)), o.w);
     }
 }
 
-// ---- exclusive scan of uint32 counts into int64 offsets ----
-__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t *total) {
-    __shared__ int64_t wsum[kScanThreads / 32];
+// ---- exclusive scan of uint32 counts (totals < 2^32) ----
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t wsum[kScanThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int64_t x = v;
+    uint32_t x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
     if (lane == 31) wsum[wid] = x;
     __syncthreads();
     if (wid == 0) {
-        int64_t s = lane < kScanThreads / 32 ? wsum[lane] : 0;
+        uint32_t s = lane < kScanThreads / 32 ? wsum[lane] : 0u;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(0xffffffffu, s, o);
+            const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
             if (lane >= o) s += y;
         }
-        if (lane < kScanThreads / 32) wsum[lane] = s;    // inclusive warp prefix
+        if (lane < kScanThreads / 32) wsum[lane] = s;
     }
     __syncthreads();
-    const int64_t before = (wid > 0 ? wsum[wid - 1] : 0) + x - v;
+    const uint32_t before = (wid > 0 ? wsum[wid - 1] : 0u) + x - v;
     *total = wsum[kScanThreads / 32 - 1];
     __syncthreads();
     return before;
 }
 
+// out may alias in: every thread reads its own elements before writing them.
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_blocks(const uint32_t *__restrict__ cnt, int64_t n, int64_t *__restrict__ off,
-              int64_t *__restrict__ bsum) {
+k_scan_blocks(const uint32_t *in, int64_t n, uint32_t *out, uint32_t *bsum) {
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
-    int64_t v[kScanPer];
-    int64_t s = 0;
+    uint32_t v[kScanPer];
+    uint32_t s = 0;
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) {
-        v[k] = base + k < n ? (int64_t)cnt[base + k] : 0;
+        v[k] = base + k < n ? in[base + k] : 0u;
         s += v[k];
     }
-    int64_t total;
-    int64_t run = block_exclusive_scan(s, &total);
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(s, &total);
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) {
-        if (base + k < n) off[base + k] = run;
+        if (base + k < n) out[base + k] = run;
         run += v[k];
     }
     if (threadIdx.x == 0) bsum[blockIdx.x] = total;
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_sums(int64_t *__restrict__ bsum, int nb, int64_t *__restrict__ grand) {
-    // one block; nb <= kScanTile
-    const int base = threadIdx.x * kScanPer;
-    int64_t v[kScanPer];
-    int64_t s = 0;
-#pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-        v[k] = base + k < nb ? bsum[base + k] : 0;
-        s += v[k];
-    }
-    int64_t total;
-    int64_t run = block_exclusive_scan(s, &total);
-#pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-        if (base + k < nb) bsum[base + k] = run;
-        run += v[k];
-    }
-    if (threadIdx.x == 0) *grand = total;
-}
-
-__global__ void __launch_bounds__(kScanThreads)
-k_scan_add(int64_t *__restrict__ off, int64_t n, const int64_t *__restrict__ bsum) {
+k_scan_add(uint32_t *__restrict__ out, int64_t n, const uint32_t *__restrict__ bsum, int nb) {
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
-    const int64_t add = bsum[blockIdx.x];
+    const uint32_t add = bsum[blockIdx.x];
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k)
-        if (base + k < n) off[base + k] += add;
+        if (base + k < n) out[base + k] += add;
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = bsum[nb];
 }
 
 // ---- tile paint ----
-// Per-axis B-spline weights of order P for a node-relative coordinate u
-// (cells): nodes base .. base + P - 1.
+// Per-axis B-spline weights of order P at node-relative coordinate u (cells):
+// nodes base .. base + P - 1.
 template <int P>
 __device__ __forceinline__ void spline_weights(float u, int &base, float *wt) {
     if (P == 2) {                       // CIC
@@ -318,9 +324,27 @@ __device__ __forceinline__ void spline_weights(float u, int &base, float *wt) {
     }
 }
 
-template <int P>
-__device__ __forceinline__ void deposit(unsigned long long *acc, int T, float x, float y, float z,
-                                        float ws) {
+// Fixed-point split of one tile: deposit q = round(v) (v = w W 2^S) is held as
+// hi * 2^B + lo with lo in [0, 2^B]; the cell keeps sum(lo) and sum(hi) in two
+// uint32 words.  With at most `ncand` deposits per cell, sum(lo) <=
+// ncand 2^B < 2^32 and |sum(hi)| <= ncand (hmax + 1) < 2^31 by construction.
+struct Split {
+    int B;            // split bit (1 .. 22)
+    float twoB;       // 2^B
+    unsigned twoB_u;  // 2^B as an integer
+    float inv2B;      // 2^-B
+    float hi_scale;   // 2^(B - S): weight units of one hi count
+    int fast;         // 2: no deposit needs a split; 1: split when needed;
+                      // 0: this tile uses 64-bit shared atomics instead
+};
+
+// MODE 2: every deposit is known to satisfy 0 <= round(v) < 2^B (unit
+// weights): one FMA, one subtract, one 32-bit shared atomic per cell.
+// MODE 1: as 2, with a split into hi * 2^B + lo for the rare large or
+// negative deposit.  MODE 0: 64-bit shared atomics (dense tiles).
+template <int P, int MODE>
+__device__ __forceinline__ void deposit(unsigned *lo, unsigned *hi, unsigned long long *acc64,
+                                        const Split &sp, int T, float x, float y, float z, float ws) {
     int bx, by, bz;
     float wx[P], wy[P], wz[P];
     spline_weights<P>(x, bx, wx);
@@ -336,65 +360,243 @@ __device__ __forceinline__ void deposit(unsigned long long *acc, int T, float x,
             const int cy = by + b;
             if ((unsigned)cy >= (unsigned)T) continue;
             const float vxy = vx * wy[b];
-            unsigned long long *row = acc + (cx * T + cy) * T;
+            const int row = (cx * T + cy) * T;
 #pragma unroll
             for (int c = 0; c < P; ++c) {
                 const int cz = bz + c;
                 if ((unsigned)cz >= (unsigned)T) continue;
-                const long long q = __float2ll_rn(vxy * wz[c]);
-                if (q != 0) atomicAdd(row + cz, (unsigned long long)q);
+                if (MODE == 2) {
+                    atomicAdd(lo + row + cz, __float_as_uint(fmaf(vxy, wz[c], 8388608.0f)) - 0x4B000000u);
+                } else if (MODE == 1) {
+                    // 2^23 + round(v) in one FMA; its bits minus 0x4B000000 are
+                    // round(v) whenever 0 <= round(v) < 2^B (B <= 22): the
+                    // common case, one 32-bit shared atomic.
+                    const unsigned q = __float_as_uint(fmaf(vxy, wz[c], 8388608.0f)) - 0x4B000000u;
+                    if (q < sp.twoB_u) {
+                        atomicAdd(lo + row + cz, q);
+                    } else {              // large or negative deposit: split hi * 2^B + lo
+                        const float v = vxy * wz[c];
+                        const float hf = floorf(v * sp.inv2B);
+                        const float lf = fmaf(-hf, sp.twoB, v);          // exact, in [0, 2^B)
+                        const unsigned ql = __float_as_uint(lf + 8388608.0f) - 0x4B000000u;
+                        atomicAdd(lo + row + cz, ql);
+                        if (hf != 0.0f)
+                            atomicAdd(hi + row + cz, (unsigned)(__float_as_int(hf + 12582912.0f) - 0x4B400000));
+                    }
+                } else {
+                    const long long q = __float2ll_rn(vxy * wz[c]);
+                    if (q) atomicAdd(acc64 + row + cz, (unsigned long long)q);
+                }
             }
         }
     }
 }
 
-template <typename M>
-__device__ __forceinline__ M fixed_to_real(unsigned long long a, int S);
-template <>
-__device__ __forceinline__ float fixed_to_real<float>(unsigned long long a, int S) {
-    return ldexpf(__ll2float_rn((long long)a), -S);
-}
-template <>
-__device__ __forceinline__ double fixed_to_real<double>(unsigned long long a, int S) {
-    return ldexp(__ll2double_rn((long long)a), -S);
+// Correctly rounded int64 -> float without the 64-bit conversion instruction.
+__device__ __forceinline__ float ll_to_float_rn(long long q) {
+    if (q == 0) return 0.0f;
+    const unsigned long long u = q < 0 ? 0ull - (unsigned long long)q : (unsigned long long)q;
+    const int nb = 64 - __clzll((long long)u);
+    float f;
+    if (nb <= 24) {
+        f = (float)(unsigned)u;
+    } else {
+        const int sh = nb - 24;
+        unsigned long long m = u >> sh;
+        const unsigned long long rem = u & ((1ull << sh) - 1ull);
+        const unsigned long long half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (m & 1ull))) ++m;
+        f = (float)(unsigned)m * __uint_as_float((unsigned)(127 + sh) << 23);
+    }
+    return q < 0 ? -f : f;
 }
 
-template <int P, int NM, typename M>
+// Cell value in weight units from its fixed-point words.  FP32: the fast path
+// rounds hi 2^(B-S) + lo 2^-S within one ulp (a fixed function of the integer
+// words, so still bit-reproducible); the 64-bit path is rounded exactly.
+// FP64: exact in both paths (the cell integer has far fewer than 53 bits).
+template <typename M>
+__device__ __forceinline__ M cell_value(unsigned lo, unsigned hi, unsigned long long a64, const Split &sp,
+                                        float inv_scale);
+template <>
+__device__ __forceinline__ float cell_value<float>(unsigned lo, unsigned hi, unsigned long long a64,
+                                                   const Split &sp, float inv_scale) {
+    if (sp.fast) return fmaf((float)(int)hi, sp.hi_scale, (float)lo * inv_scale);
+    return ll_to_float_rn((long long)a64) * inv_scale;
+}
+template <>
+__device__ __forceinline__ double cell_value<double>(unsigned lo, unsigned hi, unsigned long long a64,
+                                                     const Split &sp, float inv_scale) {
+    if (sp.fast) return fma((double)(int)hi, (double)sp.hi_scale, (double)lo * (double)inv_scale);
+    return __ll2double_rn((long long)a64) * (double)inv_scale;
+}
+
+__device__ __forceinline__ int ceil_log2(unsigned x) {     // x >= 1
+    return x <= 1u ? 0 : 32 - __clz(x - 1u);
+}
+
+// Copy candidates [k0, k0 + n) of the tile into shared memory, already in this
+// tile's frame (segment shift added) and with the weight scaled by 2^S.
+__device__ __forceinline__ void stage_candidates(const float4 *__restrict__ sorted, const uint32_t *s_beg,
+                                                 const uint32_t *s_pre, const float (*s_shift)[3],
+                                                 uint32_t k0, uint32_t n, float scale, float4 *cand) {
+    for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const uint32_t k = k0 + j;
+        int lo_s = 0, hi_s = kSegments;               // s_pre[lo_s] <= k < s_pre[hi_s]
+        while (hi_s - lo_s > 1) {
+            const int mid = (lo_s + hi_s) >> 1;
+            if (s_pre[mid] <= k) lo_s = mid;
+            else hi_s = mid;
+        }
+        const float4 v = __ldg(sorted + s_beg[lo_s] + (k - s_pre[lo_s]));
+        cand[j] = make_float4(v.x + s_shift[lo_s][0], v.y + s_shift[lo_s][1], v.z + s_shift[lo_s][2],
+                              v.w * scale);
+    }
+}
+
+template <int P, int MODE>
+__device__ __forceinline__ void deposit_staged(const float4 *cand, uint32_t n, unsigned *lo, unsigned *hi,
+                                               unsigned long long *acc64, const Split &sp, int T, float sh) {
+    for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const float4 v = cand[j];
+        deposit<P, MODE>(lo, hi, acc64, sp, T, v.x + sh, v.y + sh, v.z + sh, v.w);
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void deposit_any(const float4 *cand, uint32_t n, unsigned *lo, unsigned *hi,
+                                            unsigned long long *acc64, const Split &sp, int T, float sh) {
+    if (sp.fast == 2) deposit_staged<P, 2>(cand, n, lo, hi, acc64, sp, T, sh);
+    else if (sp.fast == 1) deposit_staged<P, 1>(cand, n, lo, hi, acc64, sp, T, sh);
+    else deposit_staged<P, 0>(cand, n, lo, hi, acc64, sp, T, sh);
+}
+
+// TC > 0: the tile edge is the compile-time constant TC (index math in shifts).
+template <int P, int NM, typename M, int TC>
 __global__ void __launch_bounds__(kPaintThreads)
-k_paint_tiles(const float4 *__restrict__ sorted, const int64_t *__restrict__ off, PaintGeom g,
-              int S, M *__restrict__ mesh, long long item_stride, long long mesh_stride,
-              int accumulate) {
-    extern __shared__ unsigned long long acc[];       // NM * T^3 fixed-point cells
-    const int T = g.T, T3 = T * T * T;
+k_paint_tiles(const float4 *__restrict__ sorted, const uint32_t *__restrict__ off, PaintGeom g,
+              int S, const unsigned *__restrict__ wmax_bits, float wmax_deposit, M *__restrict__ mesh,
+              long long item_stride, long long mesh_stride, int accumulate) {
+    extern __shared__ __align__(16) unsigned smu[];   // lo[T^3], hi[T^3] or acc64[T^3]; cand[kStage]
+    __shared__ uint32_t s_beg[kSegments];
+    __shared__ uint32_t s_pre[kSegments + 1];
+    __shared__ float s_shift[kSegments][3];
+    const int T = TC > 0 ? TC : g.T, T3 = T * T * T;
+    unsigned *lo = smu, *hi = smu + T3;
+    unsigned long long *acc64 = reinterpret_cast<unsigned long long *>(smu);
+    float4 *cand = reinterpret_cast<float4 *>(smu + 2 * T3);
+
     const int64_t gt = blockIdx.x;                    // item * ntiles + tile
     const int64_t item = gt / g.ntiles;
     const int64_t t = gt - item * g.ntiles;
     const int tx = (int)(t / ((int64_t)g.ntx * g.ntx));
     const int ty = (int)((t / g.ntx) % g.ntx);
     const int tz = (int)(t % g.ntx);
-    for (int c = threadIdx.x; c < NM * T3; c += blockDim.x) acc[c] = 0ull;
-    __syncthreads();
-    const float scale = ldexpf(1.0f, S);
-    const int64_t q1 = off[gt + 1];
-    for (int64_t q = off[gt] + threadIdx.x; q < q1; q += blockDim.x) {
-        const float4 v = __ldcs(sorted + q);
-        const float ws = v.w * scale;
-        deposit<P>(acc, T, v.x, v.y, v.z, ws);
-        if (NM == 2) deposit<P>(acc + T3, T, v.x + 0.5f, v.y + 0.5f, v.z + 0.5f, ws);
+
+    // Segments: neighbour offset d (per axis -1, 0, +1) with the classes of
+    // that neighbour whose window reaches this tile: d = -1 -> class 2,
+    // d = 0 -> any class, d = +1 -> class 0.  Index s = (ax * 5 + ay) * 3 + az
+    // with ax, ay over the 5 (d, class) pairs and az over the 3 z offsets
+    // (whose class ranges are contiguous keys).
+    if (threadIdx.x < kSegments) {
+        const int s = threadIdx.x;
+        const int ax = s / 15, ay = (s / 3) % 5, az = s % 3;
+        const int dx = ax == 0 ? -1 : (ax == 4 ? 1 : 0), cx = ax == 0 ? 2 : (ax == 4 ? 0 : ax - 1);
+        const int dy = ay == 0 ? -1 : (ay == 4 ? 1 : 0), cy = ay == 0 ? 2 : (ay == 4 ? 0 : ay - 1);
+        const int dz = az - 1;
+        const int cz0 = dz == -1 ? 2 : 0, cz1 = dz == 1 ? 0 : 2;
+        const int64_t nt = ((int64_t)wrapmod(tx + dx, g.ntx) * g.ntx + wrapmod(ty + dy, g.ntx)) * g.ntx +
+                           wrapmod(tz + dz, g.ntx);
+        const int64_t kb = ((int64_t)item * g.ntiles + nt) * kClasses + cx * 9 + cy * 3;
+        const uint32_t b = off[kb + cz0], e = off[kb + cz1 + 1];
+        s_beg[s] = b;
+        s_pre[s + 1] = e - b;
+        s_shift[s][0] = (float)(dx * T);
+        s_shift[s][1] = (float)(dy * T);
+        s_shift[s][2] = (float)(dz * T);
     }
     __syncthreads();
+    if (threadIdx.x < 32) {                          // warp scan of the 75 lengths
+        const int lane = threadIdx.x;
+        uint32_t v0 = 0, v1 = 0, v2 = 0;
+        if (3 * lane < kSegments) v0 = s_pre[3 * lane + 1];
+        if (3 * lane + 1 < kSegments) v1 = s_pre[3 * lane + 2];
+        if (3 * lane + 2 < kSegments) v2 = s_pre[3 * lane + 3];
+        uint32_t x = v0 + v1 + v2;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        const uint32_t before = x - (v0 + v1 + v2);
+        __syncwarp();
+        if (lane == 0) s_pre[0] = 0;
+        if (3 * lane < kSegments) s_pre[3 * lane + 1] = before + v0;
+        if (3 * lane + 1 < kSegments) s_pre[3 * lane + 2] = before + v0 + v1;
+        if (3 * lane + 2 < kSegments) s_pre[3 * lane + 3] = before + v0 + v1 + v2;
+    }
+    __syncthreads();
+    const uint32_t total = s_pre[kSegments];
+
+    Split sp;
+    {
+        const unsigned nc = total > 0u ? total : 1u;
+        sp.B = min(22, 31 - ceil_log2(nc));
+        sp.twoB = __uint_as_float((unsigned)(127 + max(sp.B, 0)) << 23);
+        sp.twoB_u = 1u << max(sp.B, 0);
+        sp.inv2B = __uint_as_float((unsigned)(127 - max(sp.B, 0)) << 23);
+        sp.hi_scale = ldexpf(1.0f, sp.B - S);
+        const float wmax = __uint_as_float(wmax_bits[item]);
+        const float hmax = ldexpf(wmax, S - sp.B);
+        sp.fast = sp.B >= 1 && hmax < 4194304.0f && (float)nc * (hmax + 1.0f) < 2.0e9f;
+        // wmax_deposit > 0: all weights are in [0, wmax_deposit / max W]; then
+        // no deposit reaches 2^B if wmax_deposit 2^S < 2^B - 1
+        if (sp.fast && wmax_deposit > 0.0f && ldexpf(wmax_deposit, S) < (float)(sp.twoB_u - 1u)) sp.fast = 2;
+    }
+    const float scale = ldexpf(1.0f, S);
+    const float inv_scale = ldexpf(1.0f, -S);
+    const bool staged_once = total <= (uint32_t)kStage;
+    if (staged_once) stage_candidates(sorted, s_beg, s_pre, s_shift, 0u, total, scale, cand);
     const long long pitch = 2LL * (g.N / 2 + 1);
     M *base = mesh + item * item_stride;
+
+#pragma unroll 1
     for (int m = 0; m < NM; ++m) {
-        M *mb = base + m * mesh_stride;
-        for (int c = threadIdx.x; c < T3; c += blockDim.x) {
-            const int cz = c % T, cy = (c / T) % T, cx = c / (T * T);
-            const long long gx = (long long)tx * T + cx, gy = (long long)ty * T + cy;
-            const long long idx = (gx * g.N + gy) * pitch + (long long)tz * T + cz;
-            const M val = fixed_to_real<M>(acc[m * T3 + c], S);
+        {
+            uint4 *z4 = reinterpret_cast<uint4 *>(smu);
+            const int n4 = (2 * T3) / 4;
+            for (int c = threadIdx.x; c < n4; c += blockDim.x) z4[c] = make_uint4(0u, 0u, 0u, 0u);
+            for (int c = 4 * n4 + threadIdx.x; c < 2 * T3; c += blockDim.x) smu[c] = 0u;
+        }
+        __syncthreads();
+        const float sh = m ? 0.5f : 0.0f;
+        if (staged_once) {
+            deposit_any<P>(cand, total, lo, hi, acc64, sp, T, sh);
+        } else {
+            for (uint32_t k0 = 0; k0 < total; k0 += kStage) {     // dense tile: batches
+                const uint32_t n = min((uint32_t)kStage, total - k0);
+                __syncthreads();                                  // previous batch consumed
+                stage_candidates(sorted, s_beg, s_pre, s_shift, k0, n, scale, cand);
+                __syncthreads();
+                deposit_any<P>(cand, n, lo, hi, acc64, sp, T, sh);
+            }
+        }
+        __syncthreads();
+        M *mb = base + m * mesh_stride + ((long long)tx * T * g.N + (long long)ty * T) * pitch +
+                (long long)tz * T;
+        // rows of T cells along z: thread -> (row, cz); rows (cx, cy) advance together
+        const int rows_per_pass = blockDim.x / T;
+        const int cz = threadIdx.x % T;
+        for (int r = threadIdx.x / T; r < T * T && threadIdx.x < rows_per_pass * T; r += rows_per_pass) {
+            const int cx = r / T, cy = r - cx * T;
+            const int c = r * T + cz;
+            const long long idx = ((long long)cx * g.N + cy) * pitch + cz;
+            const M val = sp.fast ? cell_value<M>(lo[c], sp.fast == 2 ? 0u : hi[c], 0ull, sp, inv_scale)
+                                  : cell_value<M>(0u, 0u, acc64[c], sp, inv_scale);
             if (accumulate) mb[idx] += val;
             else mb[idx] = val;
         }
+        __syncthreads();
     }
 }
 
@@ -407,28 +609,28 @@ __device__ __forceinline__ C cmul(C a, C b) {
     return r;
 }
 
-__device__ __forceinline__ void load4(const float2 *p, float2 *a) {
-    const float4 u = __ldcs(reinterpret_cast<const float4 *>(p));
-    const float4 v = __ldcs(reinterpret_cast<const float4 *>(p) + 1);
-    a[0] = make_float2(u.x, u.y);
-    a[1] = make_float2(u.z, u.w);
-    a[2] = make_float2(v.x, v.y);
-    a[3] = make_float2(v.z, v.w);
-}
-__device__ __forceinline__ void load4(const double2 *p, double2 *a) {
+__device__ __forceinline__ void load_vec(const float2 *p, float2 *a) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) a[k] = __ldcs(p + k);
+    for (int k = 0; k < kBinVec / 2; ++k) {
+        const float4 u = __ldcs(reinterpret_cast<const float4 *>(p) + k);
+        a[2 * k] = make_float2(u.x, u.y);
+        a[2 * k + 1] = make_float2(u.z, u.w);
+    }
+}
+__device__ __forceinline__ void load_vec(const double2 *p, double2 *a) {
+#pragma unroll
+    for (int k = 0; k < kBinVec; ++k) a[k] = __ldcs(p + k);
 }
 
 __host__ __device__ __forceinline__ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 template <typename R, typename C, typename A>
 struct BinSmem {
-    // layout: hist[nh] (A), cw_l[Nh] (R), ph_l[Nh] (C), edge[nk+1] (int)
+    // layout: hist[nh] (A), cw_l[Nh] (R), ph_l[Nh] (C), edge pairs[nk] (int2: m range of bin b)
     __host__ __device__ static size_t off_cw(const BinGeom &g) { return align_up((size_t)g.nh * sizeof(A), 16); }
     __host__ __device__ static size_t off_ph(const BinGeom &g) { return align_up(off_cw(g) + (size_t)g.Nh * sizeof(R), 16); }
     __host__ __device__ static size_t off_edge(const BinGeom &g) { return align_up(off_ph(g) + (size_t)g.Nh * sizeof(C), 16); }
-    __host__ __device__ static size_t bytes(const BinGeom &g) { return align_up(off_edge(g) + (size_t)(g.nk + 1) * sizeof(int), 16); }
+    __host__ __device__ static size_t bytes(const BinGeom &g) { return align_up(off_edge(g) + (size_t)g.nk * sizeof(int2), 16); }
 };
 
 template <bool IL, bool TWOD, bool POLES, typename R, typename C, typename A>
@@ -441,13 +643,13 @@ k_bin(const C *__restrict__ mesh, long long item_stride_c, long long mesh_stride
     A *hist = reinterpret_cast<A *>(smraw);
     R *scw = reinterpret_cast<R *>(smraw + SM::off_cw(g));
     C *sph = reinterpret_cast<C *>(smraw + SM::off_ph(g));
-    int *sedge = reinterpret_cast<int *>(smraw + SM::off_edge(g));
+    int2 *sedge = reinterpret_cast<int2 *>(smraw + SM::off_edge(g));
     for (int k = threadIdx.x; k < g.nh; k += blockDim.x) hist[k] = (A)0;
     for (int k = threadIdx.x; k < g.Nh; k += blockDim.x) {
         scw[k] = cw[k];
         sph[k] = ph[k + g.N / 2];
     }
-    for (int k = threadIdx.x; k <= g.nk; k += blockDim.x) sedge[k] = kedge[k];
+    for (int k = threadIdx.x; k < g.nk; k += blockDim.x) sedge[k] = make_int2(kedge[k], kedge[k + 1]);
     __syncthreads();
 
     const int item = blockIdx.y;
@@ -455,75 +657,138 @@ k_bin(const C *__restrict__ mesh, long long item_stride_c, long long mesh_stride
     const C *m2 = m1 + mesh_stride_c;
     const long long CH = (long long)kBinThreads * kBinVec;
     const int half = g.N / 2;
+    const int Nh = g.Nh;
+    // Start of this CTA's first chunk as (row, l); advanced by gridDim.x
+    // chunks per iteration without 64-bit division.
+    int row_base, l_base;
+    {
+        const long long f = (long long)blockIdx.x * CH;
+        row_base = (int)(f / Nh);
+        l_base = (int)(f - (long long)row_base * Nh);
+    }
+    const long long step = (long long)gridDim.x * CH;
+    const int step_rows = (int)(step / Nh), step_l = (int)(step - (long long)step_rows * Nh);
     for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
         const long long f0 = (long long)chunk * CH + (long long)kBinVec * threadIdx.x;
-        if (f0 >= g.modes) continue;
-        C a[kBinVec], b2[kBinVec];
-        load4(m1 + f0, a);
-        if (IL) load4(m2 + f0, b2);
-        const long long row = f0 / g.Nh;
-        int l = (int)(f0 - row * g.Nh);
-        int i = (int)(row / g.N);
-        int j = (int)(row - (long long)i * g.N);
-        int r2 = 0;
-        R rowcw = (R)0;
-        C rowph;
-        rowph.x = (R)0;
-        rowph.y = (R)0;
-        auto row_terms = [&]() {
-            const int ip = i < half ? i : i - g.N;
-            const int jp = j < half ? j : j - g.N;
-            r2 = ip * ip + jp * jp;
-            rowcw = cw[i] * cw[j];
-            if (IL) {
-                rowcw *= (R)0.25;
-                rowph = cmul(ph[ip + half], ph[jp + half]);
-            }
-        };
-        row_terms();
-#pragma unroll
-        for (int v = 0; v < kBinVec; ++v) {
-            if (l == g.Nh) {
-                l = 0;
-                if (++j == g.N) {
-                    j = 0;
-                    ++i;
-                }
-                row_terms();
-            }
-            const int m = r2 + l * l;
-            if (m != 0 && m >= g.mlo && m < g.mhi) {
-                int b = (int)(sqrtf((float)m) * g.kscale - g.koff);
-                b = min(max(b, 0), g.nk - 1);
-                while (b > 0 && m < sedge[b]) --b;
-                while (b < g.nk - 1 && m >= sedge[b + 1]) ++b;
-                C z = a[v];
+        if (f0 < g.modes) {
+            // (row, l) of f0: l_base + 8 tid = drow Nh + l with a float-reciprocal quotient
+            const int lt = l_base + kBinVec * (int)threadIdx.x;
+            int drow = (int)((float)lt * g.inv_Nh);
+            int l = lt - drow * Nh;
+            if (l < 0) { --drow; l += Nh; }
+            if (l >= Nh) { ++drow; l -= Nh; }
+            const int row = row_base + drow;
+            int i = (int)((float)row * g.inv_N);
+            int j = row - i * g.N;
+            if (j < 0) { --i; j += g.N; }
+            if (j >= g.N) { ++i; j -= g.N; }
+            int r2 = 0;
+            R rowcw = (R)0;
+            C rowph;
+            rowph.x = (R)0;
+            rowph.y = (R)0;
+            auto row_terms = [&]() {
+                const int ip = i < half ? i : i - g.N;
+                const int jp = j < half ? j : j - g.N;
+                r2 = ip * ip + jp * jp;
+                rowcw = cw[i] * cw[j];
                 if (IL) {
-                    const C t = cmul(rowph, sph[l]);
-                    z.x += b2[v].x * t.x - b2[v].y * t.y;
-                    z.y += b2[v].x * t.y + b2[v].y * t.x;
+                    rowcw *= (R)0.25;
+                    rowph = cmul(ph[ip + half], ph[jp + half]);
                 }
-                R pw = (z.x * z.x + z.y * z.y) * rowcw * scw[l];
-                if (l != 0 && l != half) pw += pw;
-                if (TWOD) {
-                    const int nmu = g.nmu;
-                    int q = (int)((float)(nmu * l) * rsqrtf((float)m));
-                    q = min(max(q, 0), nmu - 1);
-                    const long long rhs = (long long)nmu * nmu * l * l;
-                    while (q > 0 && (long long)q * q * m > rhs) --q;
-                    while (q < nmu - 1 && (long long)(q + 1) * (q + 1) * m <= rhs) ++q;
-                    atomicAdd(hist + b * nmu + q, (A)pw);
-                } else {
-                    atomicAdd(hist + b, (A)pw);
-                }
-                if (POLES) {
-                    const R mu2 = (R)(l * l) / (R)m;
-                    const R t2 = pw * mu2;
-                    atomicAdd(hist + g.hbase + b, (A)t2);
-                    atomicAdd(hist + g.hbase + g.nk + b, (A)(t2 * mu2));
-                }
+            };
+            row_terms();
+            // Skip (without loading) a run of modes that lies wholly outside
+            // [mlo, mhi): m grows with l inside a row.
+            if (l + kBinVec <= Nh) {
+                const int mlast = r2 + (l + kBinVec - 1) * (l + kBinVec - 1);
+                if (r2 + l * l >= g.mhi || mlast < g.mlo) goto next_chunk;
             }
-            ++l;
+            C a[kBinVec], b2[kBinVec];
+            load_vec(m1 + f0, a);
+            if (IL) load_vec(m2 + f0, b2);
+            int cur2 = -1, cur1 = -1;                 // open register runs
+            R run2 = (R)0, runm2 = (R)0, runm4 = (R)0;
+#pragma unroll
+            for (int v = 0; v < kBinVec; ++v) {
+                if (l == Nh) {
+                    l = 0;
+                    if (++j == g.N) {
+                        j = 0;
+                        ++i;
+                    }
+                    row_terms();
+                }
+                const int m = r2 + l * l;
+                if (m != 0 && m >= g.mlo && m < g.mhi) {
+                    const float rsm = rsqrtf((float)m);
+                    int b = (int)((float)m * rsm * g.kscale - g.koff);   // estimate, then exact
+                    b = min(max(b, 0), g.nk - 1);
+                    int2 e = sedge[b];
+                    while (b > 0 && m < e.x) e = sedge[--b];
+                    while (b < g.nk - 1 && m >= e.y) e = sedge[++b];
+                    C z = a[v];
+                    if (IL) {
+                        const C t = cmul(rowph, sph[l]);
+                        z.x += b2[v].x * t.x - b2[v].y * t.y;
+                        z.y += b2[v].x * t.y + b2[v].y * t.x;
+                    }
+                    R pw = (z.x * z.x + z.y * z.y) * rowcw * scw[l];
+                    if (l != 0 && l != half) pw += pw;
+                    int key = b;
+                    if (TWOD) {
+                        const int nmu = g.nmu;
+                        int q = (int)((float)(nmu * l) * rsm);
+                        q = min(max(q, 0), nmu - 1);
+                        if (g.mu32) {             // q^2 m and nmu^2 l^2 fit in 32 bits
+                            const unsigned rhs = (unsigned)(nmu * nmu) * (unsigned)(l * l);
+                            while (q > 0 && (unsigned)(q * q) * (unsigned)m > rhs) --q;
+                            while (q < nmu - 1 && (unsigned)((q + 1) * (q + 1)) * (unsigned)m <= rhs) ++q;
+                        } else {
+                            const long long rhs = (long long)nmu * nmu * l * l;
+                            while (q > 0 && (long long)q * q * m > rhs) --q;
+                            while (q < nmu - 1 && (long long)(q + 1) * (q + 1) * m <= rhs) ++q;
+                        }
+                        key = b * nmu + q;
+                    }
+                    if (key != cur2) {
+                        if (cur2 >= 0) atomicAdd(hist + cur2, (A)run2);
+                        cur2 = key;
+                        run2 = (R)0;
+                    }
+                    run2 += pw;
+                    if (POLES) {
+                        if (b != cur1) {
+                            if (cur1 >= 0) {
+                                atomicAdd(hist + g.hbase + cur1, (A)runm2);
+                                atomicAdd(hist + g.hbase + g.nk + cur1, (A)runm4);
+                            }
+                            cur1 = b;
+                            runm2 = (R)0;
+                            runm4 = (R)0;
+                        }
+                        R mu2;
+                        if (sizeof(R) == 4) mu2 = (R)__fdividef((float)(l * l), (float)m);
+                        else mu2 = (R)(l * l) / (R)m;
+                        const R t2 = pw * mu2;
+                        runm2 += t2;
+                        runm4 += t2 * mu2;
+                    }
+                }
+                ++l;
+            }
+            if (cur2 >= 0) atomicAdd(hist + cur2, (A)run2);
+            if (POLES && cur1 >= 0) {
+                atomicAdd(hist + g.hbase + cur1, (A)runm2);
+                atomicAdd(hist + g.hbase + g.nk + cur1, (A)runm4);
+            }
+        }
+    next_chunk:
+        l_base += step_l;
+        row_base += step_rows;
+        if (l_base >= Nh) {
+            l_base -= Nh;
+            ++row_base;
         }
     }
     __syncthreads();
@@ -531,42 +796,51 @@ k_bin(const C *__restrict__ mesh, long long item_stride_c, long long mesh_stride
     for (int k = threadIdx.x; k < g.nh; k += blockDim.x) out[k] = hist[k];
 }
 
+// sums2[(item * nchunk + chunk) * nh + k] = sum of the chunk's per-CTA histograms, in order.
 template <typename A>
-__global__ void k_bin_reduce(const A *__restrict__ partial, int G, int nh, double *__restrict__ sums) {
-    const int item = blockIdx.y;
+__global__ void k_bin_reduce(const A *__restrict__ partial, int G, int nh, int nchunk,
+                             double *__restrict__ sums2) {
+    const int item = blockIdx.z, chunk = blockIdx.y;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nh) return;
-    const A *p = partial + (long long)item * G * nh + k;
+    const int c0 = chunk * kReduceChunk, c1 = min(G, c0 + kReduceChunk);
+    const A *p = partial + ((long long)item * G) * nh + k;
     double s = 0.0;
-    for (int c = 0; c < G; ++c) s += (double)p[(long long)c * nh];   // fixed order
-    sums[(long long)item * nh + k] = s;
+    for (int c = c0; c < c1; ++c) s += (double)p[(long long)c * nh];
+    sums2[((long long)item * nchunk + chunk) * nh + k] = s;
 }
 
-__global__ void k_finalize(const double *__restrict__ sums, const unsigned long long *__restrict__ modes1d,
+__global__ void k_finalize(const double *__restrict__ sums2, int nchunk,
+                           const unsigned long long *__restrict__ modes1d,
                            const unsigned long long *__restrict__ modes2d,
                            const double *__restrict__ wsums, const int *__restrict__ err,
                            FinalGeom f, ResultLayout rl, double *__restrict__ res) {
     const int item = blockIdx.x;
-    const double *s = sums + (long long)item * f.nh;
+    const double *s0 = sums2 + (long long)item * nchunk * f.nh;
     double *r = res + (long long)item * f.RL;
-    const double wsum = wsums[3 * item], w2sum = wsums[3 * item + 1], wabs = wsums[3 * item + 2];
+    const double wsum = wsums[4 * item], w2sum = wsums[4 * item + 1], wabs = wsums[4 * item + 2];
     const double norm = f.L3 / (wsum * wsum);
     const double shot = f.L3 * w2sum / (wsum * wsum);
     const double sub = f.subtract_shot ? shot : 0.0;
     const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    auto S = [&](int k) {
+        double t = 0.0;
+        for (int c = 0; c < nchunk; ++c) t += s0[(long long)c * f.nh + k];
+        return t;
+    };
     for (int b = threadIdx.x; b < f.nk; b += blockDim.x) {
         double S0 = 0.0;
         if (f.twod) {
-            for (int q = 0; q < f.nmu; ++q) S0 += s[b * f.nmu + q];
+            for (int q = 0; q < f.nmu; ++q) S0 += S(b * f.nmu + q);
         } else {
-            S0 = s[b];
+            S0 = S(b);
         }
         const double cnt = (double)modes1d[b];
         double p0 = nan, p2 = nan, p4 = nan;
         if (cnt > 0.0) {
             p0 = norm * S0 / cnt - sub;
             if (f.poles) {
-                const double M2 = s[f.hbase + b], M4 = s[f.hbase + f.nk + b];
+                const double M2 = S(f.hbase + b), M4 = S(f.hbase + f.nk + b);
                 p2 = 5.0 * norm * (1.5 * M2 - 0.5 * S0) / cnt;
                 p4 = 9.0 * norm * (35.0 * M4 - 30.0 * M2 + 3.0 * S0) / (8.0 * cnt);
             }
@@ -579,7 +853,7 @@ __global__ void k_finalize(const double *__restrict__ sums, const unsigned long 
     if (f.twod) {
         for (int bq = threadIdx.x; bq < f.nk * f.nmu; bq += blockDim.x) {
             const double cnt = (double)modes2d[bq];
-            r[rl.pkmu + bq] = cnt > 0.0 ? norm * s[bq] / cnt - sub : nan;
+            r[rl.pkmu + bq] = cnt > 0.0 ? norm * S(bq) / cnt - sub : nan;
         }
     }
     if (threadIdx.x == 0) {
@@ -668,74 +942,105 @@ ResultLayout result_layout(int nk, int nmu) {
     return r;
 }
 
-cudaError_t launch_tile_count(const void *pos, int dtype, const float *w, const int64_t *item_off,
+int paint_classes() { return kClasses; }
+
+cudaError_t launch_sort_count(const void *pos, int dtype, const float *w, const int64_t *item_off,
                               int nitems, int64_t max_n, const PaintGeom &g, uint32_t *count,
-                              double *wsums, cudaStream_t st) {
+                              uint32_t *rank, double *wsums, unsigned *wmax, cudaStream_t st) {
+    dim3 grid(grid_for(max_n, kCountThreads, 1u << 20), nitems);
+    const bool weighted = w != nullptr || dtype == PK_F32X4;
+#define PK_COUNT(DT)                                                                                    \
+    if (weighted) k_sort_count<DT, true><<<grid, kCountThreads, 0, st>>>(pos, w, item_off, g, count, rank, wsums, wmax); \
+    else k_sort_count<DT, false><<<grid, kCountThreads, 0, st>>>(pos, w, item_off, g, count, rank, wsums, wmax);
+    switch (dtype) {
+    case PK_F32: PK_COUNT(PK_F32) break;
+    case PK_F64: PK_COUNT(PK_F64) break;
+    default: PK_COUNT(PK_F32X4) break;
+    }
+#undef PK_COUNT
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_scatter(const void *pos, int dtype, const float *w, const int64_t *item_off,
+                                int nitems, int64_t max_n, const PaintGeom &g, const uint32_t *off,
+                                const uint32_t *rank, float4 *sorted, int *err, cudaStream_t st) {
     dim3 grid(grid_for(max_n, kCountThreads, 1u << 20), nitems);
     switch (dtype) {
-    case PK_F32: k_tile_count<PK_F32><<<grid, kCountThreads, 0, st>>>(pos, w, item_off, g, count, wsums); break;
-    case PK_F64: k_tile_count<PK_F64><<<grid, kCountThreads, 0, st>>>(pos, w, item_off, g, count, wsums); break;
-    default: k_tile_count<PK_F32X4><<<grid, kCountThreads, 0, st>>>(pos, w, item_off, g, count, wsums); break;
+    case PK_F32: k_sort_scatter<PK_F32><<<grid, kCountThreads, 0, st>>>(pos, w, item_off, g, off, rank, sorted, err); break;
+    case PK_F64: k_sort_scatter<PK_F64><<<grid, kCountThreads, 0, st>>>(pos, w, item_off, g, off, rank, sorted, err); break;
+    default: k_sort_scatter<PK_F32X4><<<grid, kCountThreads, 0, st>>>(pos, w, item_off, g, off, rank, sorted, err); break;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_scatter(const void *pos, int dtype, const float *w,
-                                const int64_t *item_off, int nitems, int64_t max_n,
-                                const PaintGeom &g, uint32_t *count, const int64_t *off,
-                                float4 *sorted, int *err, cudaStream_t st) {
-    dim3 grid(grid_for(max_n, kCountThreads, 1u << 20), nitems);
-    switch (dtype) {
-    case PK_F32: k_tile_scatter<PK_F32><<<grid, kCountThreads, 0, st>>>(pos, w, item_off, g, count, off, sorted, err); break;
-    case PK_F64: k_tile_scatter<PK_F64><<<grid, kCountThreads, 0, st>>>(pos, w, item_off, g, count, off, sorted, err); break;
-    default: k_tile_scatter<PK_F32X4><<<grid, kCountThreads, 0, st>>>(pos, w, item_off, g, count, off, sorted, err); break;
+size_t scan_tmp_elems(int64_t n) {
+    size_t t = 0;
+    while (n > 1) {
+        const int64_t nb = (n + kScanTile - 1) / kScanTile;
+        t += (size_t)nb + 1;
+        n = nb;
     }
-    return cudaGetLastError();
+    return t + 2;
 }
 
-cudaError_t launch_scan(const uint32_t *count, int64_t n, int64_t *off, int64_t *block_tmp,
+// out[0 .. n) = exclusive scan of in, out[n] = total.  tmp: scan_tmp_elems(n).
+cudaError_t launch_scan(const uint32_t *in, int64_t n, uint32_t *out, uint32_t *tmp, int *launches,
                         cudaStream_t st) {
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
-    if (nb > kScanTile) return cudaErrorInvalidValue;
-    if (nb > 0) k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, st>>>(count, n, off, block_tmp);
-    k_scan_sums<<<1, kScanThreads, 0, st>>>(block_tmp, (int)nb, off + n);
-    if (nb > 0) k_scan_add<<<(unsigned)nb, kScanThreads, 0, st>>>(off, n, block_tmp);
+    if (nb <= 1) {
+        k_scan_blocks<<<1, kScanThreads, 0, st>>>(in, n, out, out + n);
+        *launches += 1;
+        return cudaGetLastError();
+    }
+    if (nb > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, out, tmp);
+    *launches += 1;
+    cudaError_t e = launch_scan(tmp, nb, tmp, tmp + nb + 1, launches, st);
+    if (e != cudaSuccess) return e;
+    k_scan_add<<<(unsigned)nb, kScanThreads, 0, st>>>(out, n, tmp, (int)nb);
+    *launches += 1;
     return cudaGetLastError();
 }
 
-size_t paint_smem_bytes(int T, int nmesh) {
-    return (size_t)nmesh * T * T * T * sizeof(unsigned long long);
+size_t paint_smem_bytes(int T) {
+    return (size_t)2 * T * T * T * sizeof(unsigned) + (size_t)kStage * sizeof(float4);
 }
 
 template <int P, int NM, typename M>
-static cudaError_t paint_inst(const float4 *sorted, const int64_t *off, int nitems,
-                              const PaintGeom &g, int S, void *mesh, long long item_stride,
-                              long long mesh_stride, int accumulate, cudaStream_t st) {
-    const size_t smem = paint_smem_bytes(g.T, NM);
-    cudaError_t e = set_smem(k_paint_tiles<P, NM, M>, smem);
-    if (e != cudaSuccess) return e;
+static cudaError_t paint_inst(const float4 *sorted, const uint32_t *off, int nitems,
+                              const PaintGeom &g, int S, const unsigned *wmax, float wmax_deposit,
+                              void *mesh, long long item_stride, long long mesh_stride, int accumulate,
+                              cudaStream_t st) {
+    const size_t smem = paint_smem_bytes(g.T);
     const long long nblocks = (long long)nitems * g.ntiles;
     if (nblocks <= 0) return cudaSuccess;
     if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_paint_tiles<P, NM, M><<<(unsigned)nblocks, kPaintThreads, smem, st>>>(
-        sorted, off, g, S, reinterpret_cast<M *>(mesh), item_stride, mesh_stride, accumulate);
+    auto kern = g.T == 16 ? k_paint_tiles<P, NM, M, 16> : k_paint_tiles<P, NM, M, 0>;
+    cudaError_t e = set_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)nblocks, kPaintThreads, smem, st>>>(sorted, off, g, S, wmax, wmax_deposit,
+                                                         reinterpret_cast<M *>(mesh), item_stride,
+                                                         mesh_stride, accumulate);
     return cudaGetLastError();
 }
 
-cudaError_t launch_paint_tiles(const float4 *sorted, const int64_t *off, int nitems,
+cudaError_t launch_paint_tiles(const float4 *sorted, const uint32_t *off, int nitems,
                                const PaintGeom &g, int window, int nmesh, int S, int f64,
-                               void *mesh, long long item_stride, long long mesh_stride,
-                               int accumulate, cudaStream_t st) {
+                               const unsigned *wmax, int unit_weights, void *mesh,
+                               long long item_stride, long long mesh_stride, int accumulate,
+                               cudaStream_t st) {
+    // Largest single deposit w W with unit weights: max W = (max per-axis weight)^3.
+    const float wdep = !unit_weights ? 0.0f : (window == 2 ? 1.0f : window == 3 ? 0.421875f : 0.2962963f);
 #define PK_PAINT_CASE(P)                                                                              \
     if (window == P) {                                                                                \
-        if (f64) return nmesh == 2 ? paint_inst<P, 2, double>(sorted, off, nitems, g, S, mesh,        \
+        if (f64) return nmesh == 2 ? paint_inst<P, 2, double>(sorted, off, nitems, g, S, wmax, wdep, mesh, \
                                                               item_stride, mesh_stride, accumulate, st) \
-                                   : paint_inst<P, 1, double>(sorted, off, nitems, g, S, mesh,        \
+                                   : paint_inst<P, 1, double>(sorted, off, nitems, g, S, wmax, wdep, mesh, \
                                                               item_stride, mesh_stride, accumulate, st); \
-        return nmesh == 2 ? paint_inst<P, 2, float>(sorted, off, nitems, g, S, mesh, item_stride,     \
-                                                    mesh_stride, accumulate, st)                      \
-                          : paint_inst<P, 1, float>(sorted, off, nitems, g, S, mesh, item_stride,     \
-                                                    mesh_stride, accumulate, st);                     \
+        return nmesh == 2 ? paint_inst<P, 2, float>(sorted, off, nitems, g, S, wmax, wdep, mesh,     \
+                                                    item_stride, mesh_stride, accumulate, st)         \
+                          : paint_inst<P, 1, float>(sorted, off, nitems, g, S, wmax, wdep, mesh,     \
+                                                    item_stride, mesh_stride, accumulate, st);        \
     }
     PK_PAINT_CASE(2)
     PK_PAINT_CASE(3)
@@ -796,7 +1101,7 @@ cudaError_t launch_bin(const void *mesh, int f64, int interlaced, long long item
                                               ctas_per_item, g, cw, ph, kedge, partial, st);
 }
 
-int bin_ctas_per_sm(const BinGeom &g, int f64, int interlaced) {
+int bin_ctas_per_sm(const BinGeom &g, int f64) {
     int n = 0;
     const size_t smem = bin_smem_bytes(g, f64);
     cudaError_t e;
@@ -809,24 +1114,26 @@ int bin_ctas_per_sm(const BinGeom &g, int f64, int interlaced) {
         set_smem(k, smem);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kBinThreads, smem);
     }
-    (void)interlaced;
     if (e != cudaSuccess || n < 1) n = 1;
     return n;
 }
 
+int reduce_chunks(int G) { return (G + kReduceChunk - 1) / kReduceChunk; }
+
 cudaError_t launch_bin_reduce(const void *partial, int f64, int G, int nh, int nitems,
-                              double *sums, cudaStream_t st) {
-    dim3 grid((nh + 255) / 256, nitems);
-    if (f64) k_bin_reduce<double><<<grid, 256, 0, st>>>(reinterpret_cast<const double *>(partial), G, nh, sums);
-    else k_bin_reduce<float><<<grid, 256, 0, st>>>(reinterpret_cast<const float *>(partial), G, nh, sums);
+                              double *sums2, cudaStream_t st) {
+    const int nchunk = reduce_chunks(G);
+    dim3 grid((nh + 127) / 128, nchunk, nitems);
+    if (f64) k_bin_reduce<double><<<grid, 128, 0, st>>>(reinterpret_cast<const double *>(partial), G, nh, nchunk, sums2);
+    else k_bin_reduce<float><<<grid, 128, 0, st>>>(reinterpret_cast<const float *>(partial), G, nh, nchunk, sums2);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const double *sums, const unsigned long long *modes1d,
+cudaError_t launch_finalize(const double *sums2, int G, const unsigned long long *modes1d,
                             const unsigned long long *modes2d, const double *wsums, const int *err,
                             const FinalGeom &f, int nitems, double *res, cudaStream_t st) {
     const ResultLayout rl = result_layout(f.nk, f.nmu);
-    k_finalize<<<nitems, 256, 0, st>>>(sums, modes1d, modes2d, wsums, err, f, rl, res);
+    k_finalize<<<nitems, 256, 0, st>>>(sums2, reduce_chunks(G), modes1d, modes2d, wsums, err, f, rl, res);
     return cudaGetLastError();
 }
 
@@ -840,11 +1147,8 @@ cudaError_t launch_geom_hist(const BinGeom &g, unsigned long long *H, unsigned l
 
 cudaError_t launch_geom_finalize(const BinGeom &g, const int *kedge, double kF,
                                  const unsigned long long *H, const unsigned long long *HL,
-                                 unsigned long long *modes1d, double *kmean1d,
-                                 unsigned long long *modes2d, double *kmean2d,
-                                 double *mumean2d, cudaStream_t st) {
-    (void)modes1d;
-    (void)kmean1d;
+                                 unsigned long long *modes2d, double *kmean2d, double *mumean2d,
+                                 cudaStream_t st) {
     const int nq = g.nmu > 0 ? g.nmu : 1;
     const int n = g.nk * nq;
     k_geom_finalize<<<(n + 127) / 128, 128, 0, st>>>(g, kedge, kF, H, HL, modes2d, kmean2d, mumean2d);
