@@ -197,6 +197,40 @@ pk_status pk_stage_times(pk_plan_t plan, double *ms);
  * (plan-time geometry kernels included; cuFFT's kernels and memsets not). */
 long long pk_launch_count(pk_plan_t plan);
 
+/* Binning with no device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc (code running
+ * while a framework captures a stream into a CUDA graph and owns all memory,
+ * programs whose device memory is handed out by a pool they do not control,
+ * hosts that forbid allocation after start-up).  It runs the same fused
+ * compensate + interlace + bin kernel as pk_compute on transforms the caller
+ * already holds, with every piece of scratch (per-CTA histograms and the
+ * compensation, phase and k-edge tables) in one fixed array of about 5.4 MB
+ * compiled into the library (so every GPU that loads the library holds it
+ * until the process exits).
+ *   cfg     geometry and binning as for pk_plan; precision must be PK_MESH_F32,
+ *           nmesh <= 4096, and nk * max(nmu, 1) + 2 nk <= 8192 (else PK_EINVAL);
+ *   mesh    device pointer, N x N x (N/2+1) complex64 (interleaved re, im),
+ *           the r2c transform of the painted mesh, 16-byte aligned;
+ *   mesh2   the same for the interlaced mesh (required iff cfg->interlaced);
+ *   sums    device pointer to nh doubles, overwritten: for nmu > 0, slots
+ *           [0, nk*nmu) hold sum h |d|^2 of (k, mu) bin b*nmu+q, else slots
+ *           [0, nk) hold sum h |d|^2 of k bin b; if cfg->poles_mask asks for
+ *           l = 2 or 4, the next nk slots hold sum h |d|^2 mu^2 and the nk
+ *           after them sum h |d|^2 mu^4.  d is the compensated (and
+ *           interlace-combined) transform, not yet divided by sum(w): the
+ *           power of a bin is L^3 sum / (sum(w)^2 * mode count);
+ *   cuda_stream  the stream to run on; the call only enqueues work;
+ *   err, errlen  optional buffer for a message on failure (may be NULL).
+ * The first call on a device looks up the scratch array's device address
+ * (with that device current); make that first call before any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (other streams
+ * or host threads) race and must be serialized by the caller.  Nothing in it
+ * needs to start at zero: every call rewrites what it later reads.
+ * Errors: PK_EINVAL (sizes beyond the limits above, NULL or misaligned
+ * pointers), PK_ECUDA. */
+pk_status pk_bin_static(const pk_config *cfg, const void *mesh, const void *mesh2, double *sums,
+                        void *cuda_stream, char *err, size_t errlen);
+
 /* Free everything the plan owns (waits for its stream).  NULL is a no-op. */
 pk_status pk_destroy(pk_plan_t plan);
 

@@ -38,7 +38,8 @@ PK_MESH_F32, PK_MESH_F64 = 0, 1
 WINDOWS = {"cic": PK_CIC, "tsc": PK_TSC, "pcs": PK_PCS}
 EXPORTED = ["pk_config_default", "pk_plan", "pk_paint", "pk_paint_many", "pk_compute",
             "pk_result", "pk_mesh", "pk_destroy", "pk_status_string", "pk_last_error",
-            "pk_plan_error", "pk_enable_timing", "pk_stage_times", "pk_launch_count"]
+            "pk_plan_error", "pk_enable_timing", "pk_stage_times", "pk_launch_count",
+            "pk_bin_static"]
 STAGES = ["sort", "paint", "fft", "bin", "final"]
 
 
@@ -111,6 +112,8 @@ def load():
         lib.pk_stage_times.restype = i
         lib.pk_launch_count.argtypes = [vp]
         lib.pk_launch_count.restype = ctypes.c_longlong
+        lib.pk_bin_static.argtypes = [ctypes.POINTER(pk_config), vp, vp, vp, vp, ctypes.c_char_p, ctypes.c_size_t]
+        lib.pk_bin_static.restype = i
         _lib = lib
     return _lib
 
