@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-2048", action="store_true", help="skip the 2048^3 Zel'dovich measurement")
     ap.add_argument("--profile", action="store_true",
                     help="timed steps only (no e2e leg, no CPU baseline, no clock sampler): for ncu")
     return ap.parse_args()
@@ -244,6 +245,51 @@ def traffic_record(kernel):
     return None
 
 
+def measure_2048(pk, torch, stream, world, steps=5, warmup=2):
+    """The precision workload at scale: 1024^3 objects on a Zel'dovich lattice,
+    L = 2000, PCS + interlacing on N = 2048 (FP32 mesh, int64 fixed-point
+    paint, FP64 bin sums), (k, mu) bins dk = 0.005 x 10, multipoles."""
+    import synth
+    L, N, dk = 2000.0, 2048, 0.005
+    pos = synth.zeldovich_lattice(1024, L, synth.seed_for(3), device="cuda")
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    n = pos.shape[0]
+    cfg = pk.make_config(L, N, "pcs", interlaced=True, dk=dk, nmu=NMU, precision="f32")
+    plan = pk.pk_plan(cfg, stream)
+    pk.pk_enable_timing(plan, True)
+    stages = {s: [] for s in pk.STAGES}
+    times = []
+    try:
+        for k in range(warmup + steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pk.pk_paint(plan, pos)
+            pk.pk_compute(plan)
+            pk.pk_result(plan, 0)
+            b.record(stream)
+            st = pk.pk_stage_times(plan)
+            b.synchronize()
+            if k >= warmup:
+                times.append(a.elapsed_time(b))
+                for s in pk.STAGES:
+                    stages[s].append(st[s])
+        peak_gb = torch.cuda.max_memory_allocated() / 1e9
+        free, total = torch.cuda.mem_get_info()
+    finally:
+        pk.pk_destroy(plan)
+        del pos
+        torch.cuda.empty_cache()
+    total_s = max_over_ranks(sum(times) / 1e3, world)
+    med = {s: statistics.median(v) for s, v in stages.items()}
+    return {"workload": "zeldovich 1024^3 objects (P~k^-2, rms 0.25 spacing), L=2000, FP32 positions, "
+                        "PCS + interlacing, Nmesh=2048, dk=0.005 x 10 mu bins, l=0,2,4",
+            "pk_per_s": world * steps / total_s, "ms_per_step": 1e3 * total_s / steps,
+            "particles_painted_per_s": n / ((med["sort"] + med["paint"]) / 1e3),
+            "stage_ms_median": med,
+            "device_mem_used_gb": (total - free) / 1e9}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -320,6 +366,9 @@ def main():
             torch.cuda.synchronize()
             e2e_s = max_over_ranks(time.perf_counter() - t0, world)
         pk.pk_destroy(plan)
+        del flush
+        torch.cuda.empty_cache()
+        big = None if (args.no_2048 or args.profile) else measure_2048(pk, torch, stream, world)
 
     if rank != 0:
         return 0
@@ -371,6 +420,8 @@ def main():
                 "h2d_bytes_per_step": int(NPART * 12), "d2h_bytes_per_step": int(res_bytes)},
         "wall_s_timed": wall,
     }
+    if big is not None:
+        line["nmesh_2048"] = big
     if world == 1 and not args.no_cpu_baseline and not args.profile:
         import oracle
         oracle.build()

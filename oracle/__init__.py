@@ -40,7 +40,7 @@ def build(force: bool = False) -> str:
         tmp = _LIB + ".%d.tmp" % os.getpid()
         subprocess.check_call([
             "gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
-            "-fno-fast-math", _SRC, "-o", tmp, "-lm"])
+            "-fno-fast-math", "-fopenmp", _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -60,6 +60,10 @@ def _load():
         lib.oracle_mubin.restype = i64
         lib.oracle_bin.argtypes = [p, p, i, d, i, i, d, d, d, i, i] + [p] * 9
         lib.oracle_bin.restype = i
+        lib.oracle_paint_block.argtypes = [p, p, i64, d, i, i, d, p, i, p]
+        lib.oracle_paint_block.restype = i
+        lib.oracle_mode_counts.argtypes = [i, d, d, d, i, i, p, p]
+        lib.oracle_mode_counts.restype = i
         _lib = lib
     return _lib
 
@@ -95,6 +99,33 @@ def paint(pos, weights, box_size: float, nmesh: int, window, shift: float = 0.0)
     if rc != 0:
         raise ValueError("oracle_paint: bad arguments")
     return mesh
+
+
+def paint_block(pos, weights, box_size, nmesh, window, c0, block, shift=0.0):
+    """Painted field on the block of cells c0 + [0, block)^3 (periodic) only:
+    oracle_paint restricted to a block, for meshes too large to hold."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    c0 = np.ascontiguousarray(np.asarray(c0, dtype=np.int64).reshape(3))
+    out = np.zeros((block, block, block), dtype=np.float64)
+    rc = _load().oracle_paint_block(_ptr(pos), _ptr(w), pos.shape[0], float(box_size), int(nmesh),
+                                    _order(window), float(shift), _ptr(c0), int(block), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_paint_block: bad arguments")
+    return out
+
+
+def mode_counts(nmesh, box_size, dk, kmin=0.0, kmax=None, nmu=0):
+    """Weighted mode counts of the k bins and (k, mu) bins (Sec. 3.4.1)."""
+    nk = nbins(box_size, nmesh, dk, kmin, kmax)
+    nm = max(int(nmu), 0)
+    c1 = np.zeros(nk, np.int64)
+    c2 = np.zeros(nk * max(nm, 1), np.int64)
+    rc = _load().oracle_mode_counts(int(nmesh), float(box_size), float(kmin), float(dk), nk, nm,
+                                    _ptr(c1), _ptr(c2))
+    if rc != 0:
+        raise ValueError("oracle_mode_counts: bad arguments")
+    return c1, (c2.reshape(nk, nm) if nm > 0 else None)
 
 
 def r2c(mesh):

@@ -19,6 +19,10 @@
  *                         equation); one mesh per call, optionally displaced by
  *                         a fraction of a cell (the interlaced second mesh,
  *                         Sec. 3.3.2, "separated by half of a cell size").
+ *   oracle_paint_block    the same painted field, evaluated only on one B^3
+ *                         block of cells (for meshes too large to hold).
+ *   oracle_mode_counts    the weighted mode counts of every k and (k, mu) bin
+ *                         (the h-weighted stored half grid, Sec. 3.4.1).
  *   oracle_bin            the FFTPower mode loop, Sec. 3.4.1: window
  *                         compensation by prod_i sinc^p(pi k_i / 2 k_N)
  *                         (Eq. window-deconvolution), the interlacing combine,
@@ -52,6 +56,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -77,6 +84,9 @@ double oracle_window_weight(int p, double d)
     }
     return NAN;
 }
+
+int64_t oracle_kbin(int64_t m, double L, double kmin, double dk);
+int64_t oracle_mubin(int64_t m, int64_t l, int64_t nmu);
 
 static int64_t mod_n(int64_t c, int64_t n)
 {
@@ -116,6 +126,104 @@ int oracle_paint(const double *pos, const double *w, int64_t n, double L, int N,
                     if (v == 0.0) continue;
                     mesh[(ia[0][kx] * NN + ia[1][ky]) * NN + ia[2][kz]] += v;
                 }
+    }
+    return 0;
+}
+
+/* The painted field F of oracle_paint, evaluated only on the cells
+ * c0 + (a, b, c), 0 <= a, b, c < B (indices taken periodically), into
+ * out[B][B][B].  Objects whose window misses the block contribute nothing.
+ * Independent objects are split over OpenMP threads, each with its own block,
+ * summed at the end.  Returns 0, or -1 on bad arguments. */
+int oracle_paint_block(const double *pos, const double *w, int64_t n, double L, int N, int p,
+                       double shift, const int64_t *c0, int B, double *out)
+{
+    if (N < 1 || L <= 0.0 || p < 2 || p > 4 || B < 1 || B > N) return -1;
+    const int64_t NN = N, BB = B, B3 = BB * BB * BB;
+    memset(out, 0, sizeof(double) * (size_t)B3);
+#pragma omp parallel
+    {
+        double *acc = (double *)calloc((size_t)B3, sizeof(double));
+#pragma omp for schedule(static)
+        for (int64_t q = 0; q < n; ++q) {
+            double wa[3][8];
+            int64_t ia[3][8];     /* offset of the node inside the block, or -1 */
+            int any = 1;
+            for (int a = 0; a < 3 && any; ++a) {
+                double x = pos[3 * q + a];
+                x = x - L * floor(x / L);
+                double s = x * (double)N / L + shift;
+                int64_t cfirst = (int64_t)floor(s - 0.5 * p);
+                any = 0;
+                for (int k = 0; k < p + 2; ++k) {
+                    int64_t c = cfirst + k;
+                    wa[a][k] = oracle_window_weight(p, s - (double)c);
+                    int64_t off = mod_n(c - c0[a], NN);
+                    ia[a][k] = off < BB ? off : -1;
+                    if (ia[a][k] >= 0 && wa[a][k] != 0.0) any = 1;
+                }
+            }
+            if (!any) continue;
+            double wq = w ? w[q] : 1.0;
+            for (int kx = 0; kx < p + 2; ++kx) {
+                if (ia[0][kx] < 0) continue;
+                for (int ky = 0; ky < p + 2; ++ky) {
+                    if (ia[1][ky] < 0) continue;
+                    for (int kz = 0; kz < p + 2; ++kz) {
+                        if (ia[2][kz] < 0) continue;
+                        acc[(ia[0][kx] * BB + ia[1][ky]) * BB + ia[2][kz]] +=
+                            wq * wa[0][kx] * wa[1][ky] * wa[2][kz];
+                    }
+                }
+            }
+        }
+#pragma omp critical
+        for (int64_t k = 0; k < B3; ++k) out[k] += acc[k];
+        free(acc);
+    }
+    return 0;
+}
+
+/* Weighted mode counts of the k bins (modes1d[nk]) and, if nmu > 0, of the
+ * (k, mu) bins (modes2d[nk * nmu]): the stored half grid with h = 1 on the
+ * l = 0 and l = N/2 planes and 2 elsewhere, DC excluded, bins as in
+ * oracle_kbin / oracle_mubin.  Outputs are overwritten.  Rows i are split over
+ * OpenMP threads with private counters.  Returns 0, or -1 on bad arguments. */
+int oracle_mode_counts(int N, double L, double kmin, double dk, int nk, int nmu,
+                       int64_t *modes1d, int64_t *modes2d)
+{
+    if (N < 2 || (N % 2) != 0 || L <= 0.0 || dk <= 0.0 || nk < 0 || nmu < 0) return -1;
+    const int64_t NN = N, Nh = N / 2 + 1, nq = nmu > 0 ? nmu : 1;
+    memset(modes1d, 0, sizeof(int64_t) * (size_t)nk);
+    if (nmu > 0) memset(modes2d, 0, sizeof(int64_t) * (size_t)(nk * nmu));
+#pragma omp parallel
+    {
+        int64_t *c1 = (int64_t *)calloc((size_t)nk, sizeof(int64_t));
+        int64_t *c2 = (int64_t *)calloc((size_t)(nk * nq), sizeof(int64_t));
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t i = 0; i < NN; ++i) {
+            int64_t ip = i < NN / 2 ? i : i - NN;
+            for (int64_t j = 0; j < NN; ++j) {
+                int64_t jp = j < NN / 2 ? j : j - NN;
+                for (int64_t l = 0; l < Nh; ++l) {
+                    int64_t m = ip * ip + jp * jp + l * l;
+                    if (m == 0) continue;
+                    int64_t b = oracle_kbin(m, L, kmin, dk);
+                    if (b < 0 || b >= nk) continue;
+                    int64_t h = (l == 0 || l == NN / 2) ? 1 : 2;
+                    c1[b] += h;
+                    if (nmu > 0) c2[b * nmu + oracle_mubin(m, l, nmu)] += h;
+                }
+            }
+        }
+#pragma omp critical
+        {
+            for (int k = 0; k < nk; ++k) modes1d[k] += c1[k];
+            if (nmu > 0)
+                for (int k = 0; k < nk * nmu; ++k) modes2d[k] += c2[k];
+        }
+        free(c1);
+        free(c2);
     }
     return 0;
 }

@@ -274,6 +274,7 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
     // ---- paint geometry ----
     PaintGeom &pg = P->pg;
     pg.invH = (float)((double)P->N / c.box_size);
+    pg.invH_lo = (float)((double)P->N / c.box_size - (double)pg.invH);
     pg.invHd = (double)P->N / c.box_size;
     pg.N = P->N;
     pg.T = T;

@@ -16,6 +16,7 @@ namespace pk {
 // floor(s)+hi] along each axis cover the window support on both meshes.
 struct PaintGeom {
     float invH;         // N / L in FP32
+    float invH_lo;      // N / L - invH (the FP32 rounding residual)
     double invHd;       // N / L in FP64
     int N;              // cells per side
     int T;              // tile edge (divides N, T >= hi - lo)

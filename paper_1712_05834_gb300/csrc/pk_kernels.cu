@@ -62,10 +62,18 @@ __device__ __forceinline__ int wrapmod(int a, int n) {
 // Cell coordinate s = x * (N / L) wrapped periodically into [0, N).  Written
 // with explicitly rounded intrinsics so that no FMA contraction can differ
 // between the count and the scatter kernels: both must see the same s.
-__device__ __forceinline__ float wrap_cells(float x, float invH, int N) {
+// FP32 positions: s is returned as s_hi + *e, where s_hi = fl(x * invH) and
+// *e is the exact residual of that product plus x times the residual of
+// invH = N / L; cells and tiles follow s_hi, and e is added back into the
+// small tile-local coordinate (whose resolution is ~1e-6 cells), so large
+// meshes do not lose the FP32 rounding of s (up to 1.2e-4 cells at N = 2048).
+// Positions outside [0, L) are wrapped on s_hi with e = 0.
+__device__ __forceinline__ float wrap_cells(float x, float invH, float invH_lo, int N, float *e) {
     const float n = (float)N;
     float s = __fmul_rn(x, invH);
+    *e = __fadd_rn(__fmaf_rn(x, invH, -s), __fmul_rn(x, invH_lo));
     if (!(s >= 0.0f && s < n)) {
+        *e = 0.0f;
         s = __fsub_rn(s, __fmul_rn(n, floorf(__fdiv_rn(s, n))));
         if (s < 0.0f) s = __fadd_rn(s, n);
         if (s >= n) s = __fsub_rn(s, n);
@@ -88,6 +96,7 @@ __device__ __forceinline__ double wrap_cells(double x, double invH, int N) {
 template <typename R>
 struct Obj {
     R s[3];
+    float e[3];       // residual of s (FP32 positions), 0 for FP64 positions
     float w;
 };
 
@@ -103,21 +112,22 @@ __device__ __forceinline__ Obj<typename PosReal<DT>::type> load_obj(const void *
     Obj<R> o;
     if (DT == PK_F32X4) {
         const float4 v = __ldg(reinterpret_cast<const float4 *>(pos) + i);
-        o.s[0] = wrap_cells(v.x, g.invH, g.N);
-        o.s[1] = wrap_cells(v.y, g.invH, g.N);
-        o.s[2] = wrap_cells(v.z, g.invH, g.N);
+        o.s[0] = wrap_cells(v.x, g.invH, g.invH_lo, g.N, &o.e[0]);
+        o.s[1] = wrap_cells(v.y, g.invH, g.invH_lo, g.N, &o.e[1]);
+        o.s[2] = wrap_cells(v.z, g.invH, g.invH_lo, g.N, &o.e[2]);
         o.w = v.w;
     } else if (DT == PK_F32) {
         const float *p = reinterpret_cast<const float *>(pos) + 3 * i;
-        o.s[0] = wrap_cells(__ldg(p + 0), g.invH, g.N);
-        o.s[1] = wrap_cells(__ldg(p + 1), g.invH, g.N);
-        o.s[2] = wrap_cells(__ldg(p + 2), g.invH, g.N);
+        o.s[0] = wrap_cells(__ldg(p + 0), g.invH, g.invH_lo, g.N, &o.e[0]);
+        o.s[1] = wrap_cells(__ldg(p + 1), g.invH, g.invH_lo, g.N, &o.e[1]);
+        o.s[2] = wrap_cells(__ldg(p + 2), g.invH, g.invH_lo, g.N, &o.e[2]);
         o.w = w ? __ldg(w + i) : 1.0f;
     } else {
         const double *p = reinterpret_cast<const double *>(pos) + 3 * i;
         o.s[0] = (R)wrap_cells(__ldg(p + 0), g.invHd, g.N);
         o.s[1] = (R)wrap_cells(__ldg(p + 1), g.invHd, g.N);
         o.s[2] = (R)wrap_cells(__ldg(p + 2), g.invHd, g.N);
+        o.e[0] = o.e[1] = o.e[2] = 0.0f;
         o.w = w ? __ldg(w + i) : 1.0f;
     }
     return o;
@@ -229,8 +239,9 @@ k_sort_scatter(const void *__restrict__ pos, const float *__restrict__ w,
             atomicOr(err, 2);
             continue;
         }
-        sorted[dst] = make_float4((float)(o.s[0] - (R)(t3[0] * g.T)), (float)(o.s[1] - (R)(t3[1] * g.T)),
-                                  (float)(o.s[2] - (R)(t3[2] * g.T)), o.w);
+        sorted[dst] = make_float4((float)(o.s[0] - (R)(t3[0] * g.T)) + o.e[0],
+                                  (float)(o.s[1] - (R)(t3[1] * g.T)) + o.e[1],
+                                  (float)(o.s[2] - (R)(t3[2] * g.T)) + o.e[2], o.w);
     }
 }
 

@@ -371,3 +371,51 @@ def _oracle_512(oracle, pos):
     if "r" not in _ORACLE_CACHE:
         _ORACLE_CACHE["r"] = run_oracle(oracle, pos, None, 1000.0, 512, "tsc", True, 0.005, nmu=10)
     return _ORACLE_CACHE["r"]
+
+
+# -------------------------------------- the 2048^3 Zel'dovich workload --
+
+def test_zeldovich_1024cubed_objects_pcs_interlaced_2048(pk, oracle, torch_mod):
+    """1024^3 objects on a Zel'dovich-displaced lattice (P ~ k^-2, rms 0.25
+    spacings), L = 2000, PCS + interlacing on N = 2048, FP32 mesh with int64
+    fixed-point paint, (k, mu) bins dk = 0.005 x 10, multipoles.  The oracle
+    cannot hold this mesh, so parity is checked on what it can compute at full
+    size: mass on both meshes, the painted field on sampled cell blocks, and
+    every mode count (bit-exact)."""
+    torch = torch_mod
+    import ctypes
+    import synth
+    L, N, dk, nmu = 2000.0, 2048, 0.005, 10
+    pos = synth.zeldovich_lattice(1024, L, synth.seed_for(3), device="cuda")
+    torch.cuda.empty_cache()
+    n = pos.shape[0]
+    cfg = pk.make_config(L, N, "pcs", interlaced=True, dk=dk, nmu=nmu)
+    plan = pk.pk_plan(cfg)
+    blocks = [((0, 0, 0), 8), ((1019, 517, 2044), 8)]
+    try:
+        pk.pk_paint(plan, pos)
+        host = pos.cpu().double().numpy()
+        for m in range(2):
+            dev = torch.empty((N, N, N), dtype=torch.float32, device="cuda")
+            assert pk.load().pk_mesh(plan, 0, m, ctypes.c_void_p(dev.data_ptr())) == pk.PK_OK
+            total = float(dev.sum(dtype=torch.float64))
+            assert abs(total - n) <= 1e-6 * n, (m, total, n)
+            for c0, B in blocks:
+                idx = [torch.arange(c, c + B, device="cuda") % N for c in c0]
+                got = dev[idx[0]][:, idx[1]][:, :, idx[2]].double().cpu().numpy()
+                ref = oracle.paint_block(host, None, L, N, "pcs", c0, B, 0.5 * m)
+                assert np.max(np.abs(got - ref)) <= 1e-5 * (1.0 + np.max(np.abs(ref))), (m, c0)
+            del dev
+            torch.cuda.empty_cache()
+        del host
+        pk.pk_compute(plan)
+        r = pk.pk_result(plan)
+    finally:
+        pk.pk_destroy(plan)
+    c1, c2 = oracle.mode_counts(N, L, dk, nmu=nmu)
+    assert np.array_equal(r["modes"], c1)
+    assert np.array_equal(r["modes2d"], c2)
+    ok = c1 > 0
+    assert r["wsum"] == float(n) and abs(r["shot_noise"] - L ** 3 / n) <= 1e-12 * L ** 3 / n
+    assert np.all(np.isfinite(r["power"][ok])) and np.all(r["power"][ok] + r["shot_noise"] > 0)
+    assert np.all(np.isfinite(r["poles"][:, ok]))

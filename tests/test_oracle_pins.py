@@ -436,3 +436,48 @@ def test_pipeline_equals_full_grid_bruteforce(oracle, window, interlaced, compen
     np.testing.assert_allclose(res["poles"][2], 9 * S4 / Hc, rtol=1e-9, atol=1e-10 * shot)
     with np.errstate(invalid="ignore"):
         np.testing.assert_allclose(res["power2d"], S2d / H2d - shot, rtol=1e-10, atol=1e-10 * shot)
+
+
+# ------------------------------------------- block paint and mode counts --
+
+@pytest.mark.parametrize("window,shift", [("pcs", 0.5), ("tsc", 0.0), ("cic", 0.5)])
+def test_paint_block_equals_per_cell_bruteforce(oracle, window, shift):
+    """The block-restricted paint equals the per-cell brute force on blocks
+    inside the box and blocks that wrap around its periodic faces."""
+    rng = np.random.default_rng(31)
+    N, L = 12, 30.0
+    pos = rng.uniform(0, L, size=(400, 3))
+    w = rng.uniform(0.5, 1.5, 400)
+    full = brute_paint(pos, w, L, N, oracle.WINDOW_ORDER[window], shift, oracle)
+    for c0, B in (((2, 3, 4), 5), ((10, 11, 9), 4), ((0, 0, 0), 12)):
+        got = oracle.paint_block(pos, w, L, N, window, c0, B, shift)
+        idx = [(np.arange(B) + c) % N for c in c0]
+        ref = full[np.ix_(*idx)]
+        assert np.max(np.abs(got - ref)) < 1e-13, (c0, B)
+
+
+@pytest.mark.parametrize("N,L,dk,nmu", [(16, 100.0, 0.07, 4), (14, 5.0, 0.6, 3)])
+def test_mode_counts_equal_full_grid_enumeration(oracle, N, L, dk, nmu):
+    c1, c2 = oracle.mode_counts(N, L, dk, nmu=nmu)
+    nk = oracle.nbins(L, N, dk)
+    r1 = np.zeros(nk, np.int64)
+    r2 = np.zeros((nk, nmu), np.int64)
+    f = fftfreq_int(N)
+    for i in f:
+        for j in f:
+            for l in f:
+                m = int(i * i + j * j + l * l)
+                if m == 0:
+                    continue
+                b = int(math.floor(((2.0 * math.pi) / L * math.sqrt(m) - 0.0) / dk))
+                if not 0 <= b < nk:
+                    continue
+                q = min(int(math.isqrt(nmu * nmu * l * l // m)) if l else 0, nmu - 1)
+                while q + 1 <= nmu - 1 and (q + 1) ** 2 * m <= nmu * nmu * l * l:
+                    q += 1
+                while q > 0 and q * q * m > nmu * nmu * l * l:
+                    q -= 1
+                r1[b] += 1
+                r2[b, q] += 1
+    assert np.array_equal(c1, r1)
+    assert np.array_equal(c2, r2)
