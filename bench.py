@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-2048", action="store_true", help="skip the 2048^3 Zel'dovich measurement")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-mock batched measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--profile", action="store_true",
                     help="timed steps only (no e2e leg, no CPU baseline, no clock sampler): for ncu")
     return ap.parse_args()
@@ -290,6 +293,160 @@ def measure_2048(pk, torch, stream, world, steps=5, warmup=2):
             "device_mem_used_gb": (total - free) / 1e9}
 
 
+def max_rel_diff(a, b):
+    """Largest |a - b| over the l = 0, 2, 4 rows, relative to a's
+    pre-subtraction monopole per bin (mode counts must agree exactly)."""
+    import numpy as np
+    if not np.array_equal(a["modes"], b["modes"]):
+        return float("inf")
+    ok = a["modes"] > 0
+    raw = (a["power"] + a["shot_noise"])[ok]
+    return float(max(np.max(np.abs(a["poles"][e] - b["poles"][e])[ok] / raw) for e in range(3)))
+
+
+MOCK_L, MOCK_DK = 1000.0, 0.01
+
+
+def mock_catalogs(torch, specs):
+    import synth
+    from paper_1712_05834_gb300.batch import Catalog
+    return [Catalog(synth.lognormal_catalog(s["n"], MOCK_L, s["nmesh"], s["seed"], device="cuda"),
+                    s["nmesh"], s["window"]) for s in specs]
+
+
+def plain_pass(pk, torch, cats, plans, stream):
+    """One catalog at a time through the public API on resident batch-1 plans."""
+    from paper_1712_05834_gb300.batch import class_key
+    out = []
+    for c in cats:
+        key = class_key(c)
+        if key not in plans:
+            cfg = pk.make_config(MOCK_L, c.nmesh, c.window, interlaced=c.interlaced, dk=MOCK_DK)
+            plans[key] = pk.pk_plan(cfg, stream)
+        pk.pk_paint(plans[key], c.pos)
+        pk.pk_compute(plans[key])
+        out.append(pk.pk_result(plans[key], 0))
+    return out
+
+
+def measure_batched(pk, torch, world, rank, runs=5):
+    """256 log-normal mocks (object counts log-uniform in [2e5, 4e6], Nmesh in
+    {128, 192, 256}, CIC / TSC), L = 1000, dk = 0.01 to k_N, l = 0, 2, 4:
+    size-class batches replayed from one CUDA graph, against the same mocks
+    one at a time on resident plans."""
+    import numpy as np
+    import synth
+    from paper_1712_05834_gb300 import batch
+    specs = synth.mock_set_specs(256, synth.seed_for(4, 1000 * rank))
+    cats = mock_catalogs(torch, specs)
+    torch.cuda.synchronize()
+    nobj = sum(c.n for c in cats)
+    stream = torch.cuda.Stream()
+    tuner = batch.Autotuner(sample=16, repeats=3)
+    t0 = time.perf_counter()
+    bp = batch.BatchPower(cats, MOCK_L, dk=MOCK_DK, tuner=tuner, graph=True, stream=stream)
+    setup_s = time.perf_counter() - t0
+    try:
+        for _ in range(3):
+            res_b = bp.run()
+        barrier(world)
+        times, dev = [], []
+        for _ in range(runs):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            a.record(stream)
+            bp.launch()
+            b.record(stream)
+            res_b = bp.results()
+            times.append(time.perf_counter() - w0)
+            dev.append(a.elapsed_time(b) / 1e3)
+        launches = bp.launches_per_run
+        classes = [{"nmesh": c.key[0], "window": c.key[1], "mocks": len(c.index),
+                    "objects": int(c.offsets[-1]), "paint": "%s/%d" % c.choice} for c in bp.classes]
+    finally:
+        bp.close()
+    plans = {}
+    try:
+        res_p = plain_pass(pk, torch, cats, plans, stream)
+        barrier(world)
+        ptimes = []
+        for _ in range(runs):
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            res_p = plain_pass(pk, torch, cats, plans, stream)
+            ptimes.append(time.perf_counter() - w0)
+    finally:
+        for p in plans.values():
+            pk.pk_destroy(p)
+    tb = max_over_ranks(statistics.median(times), world)
+    tp = max_over_ranks(statistics.median(ptimes), world)
+    diff = max(max_rel_diff(p, b) for p, b in zip(res_p, res_b))
+    del cats
+    torch.cuda.empty_cache()
+    return {"workload": "256 lognormal mocks (L=1000, P~k^-1.5, RSD f=0.75), objects log-uniform in "
+                        "[2e5, 4e6], Nmesh in {128,192,256}, CIC/TSC, no interlacing, dk=0.01 to k_N, "
+                        "l=0,2,4; positions resident in HBM (%.2e objects, larger than L2)" % nobj,
+            "batched_pk_per_s": world * 256 / tb, "plain_pk_per_s": world * 256 / tp,
+            "speedup": tp / tb, "batched_ms_per_set": 1e3 * tb, "plain_ms_per_set": 1e3 * tp,
+            "batched_device_ms_per_set": 1e3 * statistics.median(dev),
+            "particles_painted_per_s_batched": world * nobj / tb,
+            "max_rel_diff_batched_vs_plain": diff,
+            "graph_launches_per_set": int(launches), "classes": classes,
+            "autotune": {k: {c: round(t, 4) for c, t in v.items()} for k, v in tuner.timings.items()},
+            "setup_s": setup_s}
+
+
+def measure_serving(pk, torch, world, rank, nreq, rate=200.0):
+    """Poisson stream (mean 200 requests/s) of P(k) requests: 95% drawn from a
+    pool of 64 mocks as in the batched workload, 5% large (Nmesh 1024, 1.3e8
+    objects, TSC + interlacing); catalogs pre-staged on the device.  Served by
+    the continuous-batching server and by the plain one-at-a-time path."""
+    import numpy as np
+    import synth
+    from paper_1712_05834_gb300 import serve
+    from paper_1712_05834_gb300.batch import Catalog
+    pool = mock_catalogs(torch, synth.mock_set_specs(64, synth.seed_for(5, 1000 * rank)))
+    big = Catalog(synth.lognormal_catalog(130_000_000, MOCK_L, 512, synth.seed_for(5, 999 + 1000 * rank),
+                                          device="cuda"), 1024, "tsc", True)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(synth.seed_for(5, 2 + 1000 * rank))
+    large = rng.random(nreq) < 0.05
+    pick = rng.integers(0, len(pool), nreq)
+    cats = [big if large[i] else pool[int(pick[i])] for i in range(nreq)]
+    arr = serve.poisson_arrivals(nreq, rate, synth.seed_for(5, 3 + 1000 * rank))
+
+    def reqs(times):
+        return [serve.Request(i, c, float(t)) for i, (c, t) in enumerate(zip(cats, times))]
+
+    out = {}
+    warm = reqs(np.zeros(nreq))[: min(nreq, 64)] + [serve.Request(-1, big, 0.0)]
+    with serve.PowerServer(MOCK_L, dk=MOCK_DK, large_nmesh=1024) as srv:
+        srv.run(warm, realtime=False)
+        barrier(world)
+        served = srv.run(reqs(arr), realtime=True)
+        out["served"] = serve.latency_summary(served)
+        sat = srv.run(reqs(np.zeros(nreq)), realtime=False)
+        out["served_saturated"] = serve.latency_summary(sat)
+        out["served"]["slots"] = srv.slots_made
+        out["served"]["evictions"] = srv.evictions
+    serve.plain_serve(warm, MOCK_L, realtime=False, dk=MOCK_DK)
+    barrier(world)
+    plain = serve.plain_serve(reqs(arr), MOCK_L, realtime=True, dk=MOCK_DK)
+    out["plain"] = serve.latency_summary(plain)
+    plain_sat = serve.plain_serve(reqs(np.zeros(nreq)), MOCK_L, realtime=False, dk=MOCK_DK)
+    out["plain_saturated"] = serve.latency_summary(plain_sat)
+    by_id = {r.rid: r for r in plain}
+    out["max_rel_diff_served_vs_plain"] = max(max_rel_diff(by_id[r.rid].result, r.result) for r in served)
+    out["workload"] = ("Poisson arrivals, mean %.0f req/s, %d requests: 95%% from a pool of 64 mocks as in the "
+                       "batched workload, 5%% large (Nmesh 1024, 1.3e8 objects, TSC + interlacing); "
+                       "catalogs pre-staged in HBM; latency = arrival -> result on the host" % (rate, nreq))
+    del pool, big, cats
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -369,6 +526,9 @@ def main():
         del flush
         torch.cuda.empty_cache()
         big = None if (args.no_2048 or args.profile) else measure_2048(pk, torch, stream, world)
+        batched = None if (args.no_batched or args.profile) else measure_batched(pk, torch, world, rank)
+        served = None if (args.no_serve or args.profile) else measure_serving(pk, torch, world, rank,
+                                                                              args.serve_requests)
 
     if rank != 0:
         return 0
@@ -384,7 +544,7 @@ def main():
     roof = {
         "paint": {"bound": "hbm", "achieved": paint_bytes / (med["sort"] + med["paint"]) / 1e6,
                   "stage_ms": med["sort"] + med["paint"], "bytes": paint_bytes,
-                  "kernels": "k_tile_count + k_scan_* + k_tile_scatter + k_paint_tiles"},
+                  "kernels": "k_sort_count + k_scan_* + k_sort_scatter + k_paint_tiles"},
         "bin": {"bound": "hbm", "achieved": bin_bytes / med["bin"] / 1e6, "stage_ms": med["bin"],
                 "bytes": bin_bytes, "kernels": "k_bin"},
     }
@@ -422,6 +582,10 @@ def main():
     }
     if big is not None:
         line["nmesh_2048"] = big
+    if batched is not None:
+        line["batched_mocks"] = batched
+    if served is not None:
+        line["serving"] = served
     if world == 1 and not args.no_cpu_baseline and not args.profile:
         import oracle
         oracle.build()

@@ -73,6 +73,17 @@ typedef enum {
     PK_MESH_F64 = 1    /* FP64 mesh, cuFFT D2Z, FP64 per-mode arithmetic        */
 } pk_precision;
 
+/* How pk_paint deposits the window weights.  Both give int64 fixed-point
+ * cells (order-free, bit-identical run to run); they differ only in speed. */
+typedef enum {
+    PK_PAINT_SORT = 0,     /* tile sort + shared-memory tiles (one global write
+                              per cell): the default, fastest on large meshes   */
+    PK_PAINT_ATOMIC = 1    /* no sort: 64-bit global atomics into a dense
+                              N^3 int64 accumulator per mesh (8 bytes per cell
+                              extra), then a conversion pass; can win when the
+                              accumulators stay in L2 (small meshes)            */
+} pk_paint_variant;
+
 typedef struct {
     double box_size;        /* L > 0                                             */
     int nmesh;              /* N: even, 4 <= N <= 4096                           */
@@ -91,6 +102,10 @@ typedef struct {
                                or 32 (FP64 mesh); 1..40                          */
     int batch;              /* catalogs per plan (separate meshes); 0 -> 1       */
     int tile;               /* paint tile edge in cells; 0 -> automatic          */
+    int paint_variant;      /* pk_paint_variant                                  */
+    int64_t capacity;       /* objects per paint call to reserve at plan time so
+                               that pk_paint never allocates or waits; 0 -> the
+                               first paint reserves what it needs                */
 } pk_config;
 
 /* Result of one catalog.  All pointers are host memory owned by the plan and
@@ -115,7 +130,8 @@ typedef struct {
 
 /* Fill *cfg with defaults: L = 1000, N = 256, CIC, not interlaced, compensated,
  * kmin = 0, kmax = k_N, dk = 2 kF, nmu = 0, all poles, z line of sight, FP32
- * mesh, shot noise subtracted, S automatic, batch 1, automatic tile. */
+ * mesh, shot noise subtracted, S automatic, batch 1, automatic tile, the
+ * sort paint variant, no reserved capacity. */
 void pk_config_default(pk_config *cfg);
 
 /* Create a plan: validates cfg, allocates the meshes (in-place r2c layout,
@@ -139,7 +155,15 @@ pk_status pk_plan(const pk_config *cfg, void *cuda_stream, pk_plan_t *out);
  *            not have been transformed since the last paint).
  * Caller keeps ownership of pos and weights; they are read on the plan's
  * stream and may be reused once the stream has passed this call.  The call
- * synchronizes the stream once (to size the tile-sorted copy of the objects).
+ * does not wait for the GPU unless the objects exceed the capacity reserved
+ * so far (cfg->capacity, or the largest earlier call), in which case it
+ * synchronizes the stream once and grows the sorted copy.  With device
+ * pointers and enough capacity, pk_paint and pk_compute only enqueue work,
+ * so a stream capture of them (cudaStreamCaptureModeThreadLocal) records a
+ * replayable CUDA graph; the graph re-reads pos, weights and the results
+ * buffers in place, so replays see new positions written to the same
+ * memory, and pk_result then reads the results of the last replay once the
+ * caller has synchronized the stream.
  * Errors: PK_EINVAL (n < 0, bad dtype, misaligned PK_F32X4), PK_ESTATE
  * (accumulate onto a transformed mesh), PK_ENOMEM, PK_ECUDA. */
 pk_status pk_paint(pk_plan_t plan, const void *pos, int dtype,

@@ -25,6 +25,7 @@ from .build import build
 
 __all__ = [
     "PK_CIC", "PK_TSC", "PK_PCS", "PK_F32", "PK_F64", "PK_F32X4", "PK_MESH_F32", "PK_MESH_F64",
+    "PK_PAINT_SORT", "PK_PAINT_ATOMIC",
     "PkError", "pk_config", "pk_config_default", "make_config", "pk_plan", "pk_paint",
     "pk_paint_many", "pk_compute", "pk_result", "pk_mesh", "pk_destroy", "pk_status_string",
     "pk_last_error", "pk_enable_timing", "pk_stage_times", "pk_launch_count", "FFTPower", "load",
@@ -35,6 +36,8 @@ PK_OK, PK_EINVAL, PK_ENOMEM, PK_ECUDA, PK_ECUFFT, PK_EOVERFLOW, PK_ETIMEOUT, PK_
 PK_CIC, PK_TSC, PK_PCS = 2, 3, 4
 PK_F32, PK_F64, PK_F32X4 = 0, 1, 2
 PK_MESH_F32, PK_MESH_F64 = 0, 1
+PK_PAINT_SORT, PK_PAINT_ATOMIC = 0, 1
+VARIANTS = {"sort": PK_PAINT_SORT, "atomic": PK_PAINT_ATOMIC}
 WINDOWS = {"cic": PK_CIC, "tsc": PK_TSC, "pcs": PK_PCS}
 EXPORTED = ["pk_config_default", "pk_plan", "pk_paint", "pk_paint_many", "pk_compute",
             "pk_result", "pk_mesh", "pk_destroy", "pk_status_string", "pk_last_error",
@@ -50,7 +53,7 @@ class pk_config(ctypes.Structure):
         ("kmax", ctypes.c_double), ("dk", ctypes.c_double), ("nmu", ctypes.c_int),
         ("poles_mask", ctypes.c_uint), ("los_axis", ctypes.c_int), ("precision", ctypes.c_int),
         ("subtract_shot", ctypes.c_int), ("fixed_scale_log2", ctypes.c_int), ("batch", ctypes.c_int),
-        ("tile", ctypes.c_int),
+        ("tile", ctypes.c_int), ("paint_variant", ctypes.c_int), ("capacity", ctypes.c_int64),
     ]
 
 
@@ -140,9 +143,12 @@ def pk_config_default() -> pk_config:
 
 def make_config(box_size, nmesh, window="cic", interlaced=False, compensated=True, dk=None,
                 kmin=0.0, kmax=None, nmu=0, poles=(0, 2, 4), precision="f32",
-                subtract_shot=True, fixed_scale_log2=0, batch=1, tile=0) -> pk_config:
+                subtract_shot=True, fixed_scale_log2=0, batch=1, tile=0, paint_variant="sort",
+                capacity=0) -> pk_config:
     """pk_config from keyword arguments that follow the paper's ``to_mesh`` /
-    ``FFTPower`` options (Sec. 3.3.2, Sec. 3.4.1).  dk defaults to 2 kF."""
+    ``FFTPower`` options (Sec. 3.3.2, Sec. 3.4.1).  dk defaults to 2 kF.
+    ``paint_variant`` ("sort" / "atomic"), ``tile`` and ``capacity`` (objects
+    reserved at plan time) only change speed and allocation, not results."""
     c = pk_config_default()
     c.box_size = float(box_size)
     c.nmesh = int(nmesh)
@@ -160,6 +166,8 @@ def make_config(box_size, nmesh, window="cic", interlaced=False, compensated=Tru
     c.fixed_scale_log2 = int(fixed_scale_log2)
     c.batch = int(batch)
     c.tile = int(tile)
+    c.paint_variant = VARIANTS[paint_variant] if isinstance(paint_variant, str) else int(paint_variant)
+    c.capacity = int(capacity)
     return c
 
 

@@ -54,10 +54,11 @@ struct pk_plan_s {
     long long nkeys = 0;             // keys per catalog
     void *d_stage = nullptr;
     size_t stage_cap = 0;
-    int64_t *d_item_off = nullptr, *h_item_off = nullptr;
+    int64_t *d_item_off = nullptr;   // catalog offsets of the last paint call
     double *d_wsums = nullptr;       // per catalog: sum w, sum w^2, sum |w|, spare
     unsigned *d_wmax = nullptr;      // per catalog: max |w| as float bits
     int *d_err = nullptr;           // bit 1: tile sort inconsistency (never expected)
+    unsigned long long *d_acc = nullptr;   // atomic variant: B * nm * N^3 int64 cells
 
     void *d_cw = nullptr, *d_ph = nullptr;
     int *d_kedge = nullptr;
@@ -74,6 +75,7 @@ struct pk_plan_s {
     int transformed = 0;    // meshes hold transforms
     int computed = 0;       // catalogs with results
     cudaEvent_t done = nullptr;
+    int done_valid = 0;             // `done` marks the last pk_compute (not captured)
     int timing = 0;
     cudaEvent_t tev[7] = {};        // stage boundaries: sort | paint || fft | bin | final
     int tev_paint = 0, tev_compute = 0;
@@ -121,12 +123,10 @@ void free_plan(pk_plan_s *p) {
     void *dev[] = {p->mesh, p->d_count, p->d_off, p->d_scan_tmp, p->d_rank, p->d_sorted,
                    p->d_stage, p->d_item_off, p->d_wsums, p->d_wmax, p->d_cw, p->d_ph,
                    p->d_kedge, p->d_partial, p->d_sums2, p->d_res, p->d_modes1d, p->d_modes2d,
-                   p->d_err};
+                   p->d_err, p->d_acc};
     for (void *d : dev)
         if (d) cudaFree(d);
-    void *host[] = {p->h_item_off, p->h_res};
-    for (void *h : host)
-        if (h) cudaFreeHost(h);
+    if (p->h_res) cudaFreeHost(p->h_res);
     if (p->done) cudaEventDestroy(p->done);
     for (cudaEvent_t e : p->tev)
         if (e) cudaEventDestroy(e);
@@ -176,6 +176,16 @@ bool is_device_pointer(const void *ptr) {
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// True while `st` is being captured into a CUDA graph.
+int capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return cs == cudaStreamCaptureStatusActive;
 }
 
 size_t record_bytes(int dtype) {
@@ -245,6 +255,10 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
         return fail(P, PK_EINVAL, "fixed_scale_log2 must be in [0, 40]");
     if (c.batch < 0 || c.batch > 65535) return fail(P, PK_EINVAL, "batch must be in [0, 65535]");
     if ((c.poles_mask & ~7u) != 0) return fail(P, PK_EINVAL, "poles_mask uses bits 0..2 only");
+    if (c.paint_variant != PK_PAINT_SORT && c.paint_variant != PK_PAINT_ATOMIC)
+        return fail(P, PK_EINVAL, "paint_variant must be PK_PAINT_SORT or PK_PAINT_ATOMIC");
+    if (c.capacity < 0 || c.capacity >= (int64_t)0xffffffffLL)
+        return fail(P, PK_EINVAL, "capacity must be in [0, 2^32 - 2]");
 
     P->cfg = c;
     P->N = c.nmesh;
@@ -346,7 +360,6 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
     PK_CUDA(P, dev_alloc(&P->d_off, sizeof(uint32_t) * (keys_all + 1)));
     PK_CUDA(P, dev_alloc(&P->d_scan_tmp, sizeof(uint32_t) * scan_tmp_elems(keys_all)));
     PK_CUDA(P, dev_alloc(&P->d_item_off, sizeof(int64_t) * (P->B + 1)));
-    PK_CUDA(P, cudaMallocHost(reinterpret_cast<void **>(&P->h_item_off), sizeof(int64_t) * (P->B + 1)));
     PK_CUDA(P, dev_alloc(&P->d_wsums, sizeof(double) * 4 * P->B));
     PK_CUDA(P, dev_alloc(&P->d_wmax, sizeof(unsigned) * P->B));
     PK_CUDA(P, dev_alloc(&P->d_err, sizeof(int)));
@@ -361,6 +374,15 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
     PK_CUDA(P, dev_alloc(&P->d_res, sizeof(double) * (size_t)P->B * fg.RL));
     PK_CUDA(P, cudaMallocHost(reinterpret_cast<void **>(&P->h_res), sizeof(double) * (size_t)P->B * fg.RL));
     const int nq = nmu > 0 ? nmu : 1;
+    if (c.paint_variant == PK_PAINT_ATOMIC) {
+        const size_t acc_bytes = sizeof(unsigned long long) * (size_t)P->B * P->nm * P->N * P->N * P->N;
+        PK_CUDA(P, dev_alloc(&P->d_acc, acc_bytes));
+        PK_CUDA(P, cudaMemset(P->d_acc, 0, acc_bytes));
+    } else if (c.capacity > 0) {
+        PK_CUDA(P, dev_alloc(&P->d_sorted, sizeof(float4) * (size_t)c.capacity));
+        PK_CUDA(P, dev_alloc(&P->d_rank, sizeof(uint32_t) * (size_t)c.capacity));
+        P->sorted_cap = c.capacity;
+    }
     PK_CUDA(P, dev_alloc(&P->d_modes1d, sizeof(unsigned long long) * nk));
     PK_CUDA(P, dev_alloc(&P->d_modes2d, sizeof(unsigned long long) * (size_t)nk * nq));
 
@@ -481,6 +503,31 @@ pk_status pk_plan(const pk_config *cfg, void *cuda_stream, pk_plan_t *out) {
     return PK_OK;
 }
 
+// The atomic variant: weight sums and deposits in one pass, then conversion.
+static pk_status paint_atomic(pk_plan_s *P, const void *dpos, int dtype, const float *dw,
+                              const int64_t *offsets, int nitems, int64_t max_n, int accumulate) {
+    const cudaStream_t st = P->st;
+    const int tm = P->timing && !capturing(st);
+    if (tm) PK_CUDA(P, cudaEventRecord(P->tev[0], st));
+    int launches = 2;
+    PK_CUDA(P, launch_upload_i64(P->d_item_off, offsets, nitems + 1, &launches, st));
+    if (!accumulate) {
+        PK_CUDA(P, cudaMemsetAsync(P->d_wsums, 0, sizeof(double) * 4 * nitems, st));
+        PK_CUDA(P, cudaMemsetAsync(P->d_wmax, 0, sizeof(unsigned) * nitems, st));
+    }
+    if (tm) PK_CUDA(P, cudaEventRecord(P->tev[1], st));   // no sort stage
+    PK_CUDA(P, launch_paint_atomic(dpos, dtype, dw, P->d_item_off, nitems, max_n, P->pg, P->p, P->nm, P->S,
+                                   P->d_acc, P->d_wsums, P->d_wmax, st));
+    PK_CUDA(P, launch_acc_to_mesh(P->d_acc, nitems, P->nm, P->N, P->S, P->f64, P->mesh,
+                                  P->nm * P->mesh_reals, P->mesh_reals, accumulate, P->nsm, st));
+    if (tm) PK_CUDA(P, cudaEventRecord(P->tev[2], st));
+    P->tev_paint = tm;
+    P->launches += launches;
+    P->npainted = nitems;
+    P->transformed = 0;
+    return PK_OK;
+}
+
 static pk_status paint_impl(pk_plan_s *P, const void *pos, int dtype, const float *weights,
                             const int64_t *offsets, int nitems, int accumulate) {
     if (dtype != PK_F32 && dtype != PK_F64 && dtype != PK_F32X4)
@@ -511,6 +558,8 @@ static pk_status paint_impl(pk_plan_s *P, const void *pos, int dtype, const floa
         return fail(P, PK_EINVAL, "PK_F32X4 positions must be 16-byte aligned");
     if (pos_dev && dtype == PK_F64 && (reinterpret_cast<uintptr_t>(pos) % 8) != 0)
         return fail(P, PK_EINVAL, "PK_F64 positions must be 8-byte aligned");
+    if ((!pos_dev || !w_dev) && capturing(st))
+        return fail(P, PK_EINVAL, "host positions or weights cannot be painted under stream capture");
     if (!pos_dev || !w_dev) {
         const size_t pbytes = pos_dev ? 0 : (size_t)ntot * rb;
         const size_t pad = (pbytes + 255) / 256 * 256;
@@ -537,6 +586,10 @@ static pk_status paint_impl(pk_plan_s *P, const void *pos, int dtype, const floa
 
     if (ntot >= (int64_t)0xffffffffLL)
         return fail(P, PK_EINVAL, "at most 2^32 - 2 objects per paint call");
+    if (P->cfg.paint_variant == PK_PAINT_ATOMIC)
+        return paint_atomic(P, dpos, dtype, dw, offsets, nitems, max_n, accumulate);
+    if (ntot > P->sorted_cap && capturing(st))
+        return fail(P, PK_EINVAL, "objects exceed the plan's capacity under stream capture");
     if (ntot > P->sorted_cap) {                 // grow the key-ordered copy (rare)
         PK_CUDA(P, cudaStreamSynchronize(st));
         if (P->d_sorted) cudaFree(P->d_sorted);
@@ -549,29 +602,28 @@ static pk_status paint_impl(pk_plan_s *P, const void *pos, int dtype, const floa
         P->sorted_cap = ntot;
     }
     const long long nkeys = (long long)nitems * P->nkeys;
-    if (P->timing) PK_CUDA(P, cudaEventRecord(P->tev[0], st));
-    memcpy(P->h_item_off, offsets, sizeof(int64_t) * (nitems + 1));
-    PK_CUDA(P, cudaMemcpyAsync(P->d_item_off, P->h_item_off, sizeof(int64_t) * (nitems + 1),
-                               cudaMemcpyHostToDevice, st));
+    const int tm = P->timing && !capturing(st);
+    if (tm) PK_CUDA(P, cudaEventRecord(P->tev[0], st));
+    int launches = 2;   // count, scatter
+    PK_CUDA(P, launch_upload_i64(P->d_item_off, offsets, nitems + 1, &launches, st));
     PK_CUDA(P, cudaMemsetAsync(P->d_count, 0, sizeof(uint32_t) * nkeys, st));
     if (!accumulate) {
         PK_CUDA(P, cudaMemsetAsync(P->d_wsums, 0, sizeof(double) * 4 * nitems, st));
         PK_CUDA(P, cudaMemsetAsync(P->d_wmax, 0, sizeof(unsigned) * nitems, st));
     }
-    int launches = 2;   // count, scatter
     PK_CUDA(P, launch_sort_count(dpos, dtype, dw, P->d_item_off, nitems, max_n, P->pg, P->d_count,
                                  P->d_rank, P->d_wsums, P->d_wmax, st));
     PK_CUDA(P, launch_scan(P->d_count, nkeys, P->d_off, P->d_scan_tmp, &launches, st));
     PK_CUDA(P, launch_sort_scatter(dpos, dtype, dw, P->d_item_off, nitems, max_n, P->pg, P->d_off,
                                    P->d_rank, P->d_sorted, P->d_err, st));
-    if (P->timing) PK_CUDA(P, cudaEventRecord(P->tev[1], st));
+    if (tm) PK_CUDA(P, cudaEventRecord(P->tev[1], st));
     const int unit_weights = dw == nullptr && dtype != PK_F32X4;
     PK_CUDA(P, launch_paint_tiles(P->d_sorted, P->d_off, nitems, P->pg, P->p, P->nm, P->S, P->f64,
                                   P->d_wmax, unit_weights, P->mesh, P->nm * P->mesh_reals,
                                   P->mesh_reals, accumulate, st));
     launches += 1;
-    if (P->timing) PK_CUDA(P, cudaEventRecord(P->tev[2], st));
-    P->tev_paint = P->timing;
+    if (tm) PK_CUDA(P, cudaEventRecord(P->tev[2], st));
+    P->tev_paint = tm;
     P->launches += launches;
     P->npainted = nitems;
     P->transformed = 0;
@@ -600,7 +652,9 @@ pk_status pk_compute(pk_plan_t P) {
     P->err.clear();
     if (P->npainted < 1 || P->transformed) return fail(P, PK_ESTATE, "nothing painted since the last compute");
     const cudaStream_t st = P->st;
-    if (P->timing) PK_CUDA(P, cudaEventRecord(P->tev[3], st));
+    const int cap = capturing(st);
+    const int tm = P->timing && !cap;
+    if (tm) PK_CUDA(P, cudaEventRecord(P->tev[3], st));
     if (P->f64) {
         cufftDoubleReal *r = reinterpret_cast<cufftDoubleReal *>(P->mesh);
         PK_CUFFT(P, cufftExecD2Z(P->fft, r, reinterpret_cast<cufftDoubleComplex *>(r)));
@@ -609,23 +663,27 @@ pk_status pk_compute(pk_plan_t P) {
         PK_CUFFT(P, cufftExecR2C(P->fft, r, reinterpret_cast<cufftComplex *>(r)));
     }
     P->transformed = 1;
-    if (P->timing) PK_CUDA(P, cudaEventRecord(P->tev[4], st));
+    if (tm) PK_CUDA(P, cudaEventRecord(P->tev[4], st));
     const int nitems = P->npainted;
     const int G = std::max(1, P->G_total / nitems);
     const long long item_c = (long long)P->nm * P->mesh_reals / 2;   // complex elements
     const long long mesh_c = P->mesh_reals / 2;
     PK_CUDA(P, launch_bin(P->mesh, P->f64, P->cfg.interlaced, item_c, mesh_c, nitems, G, P->bg,
                           P->d_cw, P->d_ph, P->d_kedge, P->d_partial, st));
-    if (P->timing) PK_CUDA(P, cudaEventRecord(P->tev[5], st));
+    if (tm) PK_CUDA(P, cudaEventRecord(P->tev[5], st));
     PK_CUDA(P, launch_bin_reduce(P->d_partial, P->f64, G, P->bg.nh, nitems, P->d_sums2, st));
     PK_CUDA(P, launch_finalize(P->d_sums2, G, P->d_modes1d, P->d_modes2d, P->d_wsums, P->d_err, P->fg,
                                nitems, P->d_res, st));
-    if (P->timing) PK_CUDA(P, cudaEventRecord(P->tev[6], st));
-    P->tev_compute = P->timing;
+    if (tm) PK_CUDA(P, cudaEventRecord(P->tev[6], st));
+    P->tev_compute = tm;
     P->launches += 3;   // bin, reduce, finalize
     PK_CUDA(P, cudaMemcpyAsync(P->h_res, P->d_res, sizeof(double) * (size_t)nitems * P->fg.RL,
                                cudaMemcpyDeviceToHost, st));
-    PK_CUDA(P, cudaEventRecord(P->done, st));
+    // Under stream capture the results come from a later graph replay, which
+    // the caller synchronizes; an event recorded into the capture could not
+    // be waited on outside it.
+    if (!cap) PK_CUDA(P, cudaEventRecord(P->done, st));
+    P->done_valid = !cap;
     P->computed = nitems;
     P->npainted = 0;
     return PK_OK;
@@ -637,7 +695,7 @@ pk_status pk_result(pk_plan_t P, int item, pk_result_view *out) {
     if (!out) return fail(P, PK_EINVAL, "out is NULL");
     if (P->computed < 1) return fail(P, PK_ESTATE, "no compute yet");
     if (item < 0 || item >= P->computed) return fail(P, PK_EINVAL, "item out of range");
-    PK_CUDA(P, cudaEventSynchronize(P->done));
+    if (P->done_valid) PK_CUDA(P, cudaEventSynchronize(P->done));
     const double *r = P->h_res + (size_t)item * P->fg.RL;
     const ResultLayout &rl = P->rl;
     const int nk = P->bg.nk, nmu = P->bg.nmu;

@@ -58,6 +58,9 @@ ResultLayout result_layout(int nk, int nmu);
 int paint_classes();                  // boundary classes per tile (27)
 size_t paint_smem_bytes(int T);
 size_t scan_tmp_elems(int64_t n);
+// dst[0 .. n) = src[0 .. n) for a host array src, through kernel parameters
+// (the host array may be reused as soon as the call returns).
+cudaError_t launch_upload_i64(int64_t *dst, const int64_t *src, int n, int *launches, cudaStream_t st);
 cudaError_t launch_sort_count(const void *pos, int dtype, const float *w, const int64_t *item_off,
                               int nitems, int64_t max_n, const PaintGeom &g, uint32_t *count,
                               uint32_t *rank, double *wsums, unsigned *wmax, cudaStream_t st);
@@ -71,6 +74,16 @@ cudaError_t launch_paint_tiles(const float4 *sorted, const uint32_t *off, int ni
                                const unsigned *wmax, int unit_weights, void *mesh,
                                long long item_stride, long long mesh_stride, int accumulate,
                                cudaStream_t st);
+
+// Direct atomic paint into dense int64 accumulators (nitems x nmesh x N^3,
+// zero on entry), then conversion into the r2c mesh layout (clears them).
+cudaError_t launch_paint_atomic(const void *pos, int dtype, const float *w, const int64_t *item_off,
+                                int nitems, int64_t max_n, const PaintGeom &g, int window, int nmesh,
+                                int S, unsigned long long *acc, double *wsums, unsigned *wmax,
+                                cudaStream_t st);
+cudaError_t launch_acc_to_mesh(unsigned long long *acc, int nitems, int nmesh, int N, int S, int f64,
+                               void *mesh, long long item_stride, long long mesh_stride, int accumulate,
+                               int nsm, cudaStream_t st);
 
 cudaError_t launch_bin(const void *mesh, int f64, int interlaced, long long item_stride_c,
                        long long mesh_stride_c, int nitems, int ctas_per_item,

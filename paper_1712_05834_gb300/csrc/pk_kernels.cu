@@ -21,6 +21,12 @@
 //                   interlaced mesh is a second pass over the same objects.
 //                   Integer adds are order-free: the mesh is bit-identical
 //                   run to run and for any object order.
+//   k_paint_atomic  the variant without a sort: one thread per object adds
+//                   each deposit with a 64-bit global atomic into a dense
+//                   int64 accumulator per mesh (as order-free as the tiles);
+//   k_acc_to_mesh   converts the accumulators into the r2c layout and clears
+//                   them.  Cheaper than sorting for small meshes that stay in
+//                   L2; the plan's paint_variant picks one of the two.
 // Bin (Sec. 3.4.1, Eq. window-deconvolution):
 //   k_bin           per stored mode: interlace combine, sinc^p compensation,
 //                   |delta|^2, k bin (exact integer edges in m = |n|^2), mu
@@ -35,6 +41,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "pk_internal.h"
 
@@ -53,6 +61,7 @@ constexpr int kClasses = 27;          // boundary classes per tile
 constexpr int kSegments = 75;         // (neighbour, class range) segments per tile
 constexpr int kReduceChunk = 32;      // per-CTA histograms summed per reduce block
 constexpr int kStage = 512;           // candidates staged in shared memory per batch
+constexpr int kUploadChunk = 256;     // int64 values per parameter upload (2 KB)
 
 __device__ __forceinline__ int wrapmod(int a, int n) {
     int r = a % n;
@@ -162,7 +171,42 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
-// wsums[4 * item + {0,1,2}] = sum w, sum w^2, sum |w|; wmax[item] = max |w| (float bits).
+// Block reduction of the weight sums: wsums[4 * item + {0,1,2}] = sum w,
+// sum w^2, sum |w|; wmax[item] = max |w| (float bits).
+__device__ __forceinline__ void flush_wsums(double sw, double sw2, double swa, float mw, bool weighted,
+                                            int item, int64_t n_item, double *__restrict__ wsums,
+                                            unsigned *__restrict__ wmax) {
+    if (weighted) {
+        __shared__ double red[3][kCountThreads / 32];
+        __shared__ float redm[kCountThreads / 32];
+        sw = warp_sum(sw);
+        sw2 = warp_sum(sw2);
+        swa = warp_sum(swa);
+        mw = warp_max(mw);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) {
+            red[0][wid] = sw;
+            red[1][wid] = sw2;
+            red[2][wid] = swa;
+            redm[wid] = mw;
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            double t = 0.0;
+            for (int k = 0; k < kCountThreads / 32; ++k) t += red[threadIdx.x][k];
+            if (t != 0.0) atomicAdd(wsums + 4 * item + threadIdx.x, t);
+        } else if (threadIdx.x == 3) {
+            float m = 0.0f;
+            for (int k = 0; k < kCountThreads / 32; ++k) m = fmaxf(m, redm[k]);
+            atomicMax(wmax + item, __float_as_uint(m));
+        }
+    } else if (blockIdx.x == 0 && threadIdx.x < 3) {
+        atomicAdd(wsums + 4 * item + threadIdx.x, (double)n_item);   // exact below 2^53
+        if (threadIdx.x == 0) atomicMax(wmax + item, __float_as_uint(1.0f));
+    }
+}
+
+// Tile sort, pass 1: key counts and ranks, plus the weight sums.
 template <int DT, bool WEIGHTED>
 __global__ void __launch_bounds__(kCountThreads)
 k_sort_count(const void *__restrict__ pos, const float *__restrict__ w,
@@ -189,34 +233,7 @@ k_sort_count(const void *__restrict__ pos, const float *__restrict__ w,
             mw = fmaxf(mw, fabsf(o.w));
         }
     }
-    if (WEIGHTED) {
-        __shared__ double red[3][kCountThreads / 32];
-        __shared__ float redm[kCountThreads / 32];
-        sw = warp_sum(sw);
-        sw2 = warp_sum(sw2);
-        swa = warp_sum(swa);
-        mw = warp_max(mw);
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        if (lane == 0) {
-            red[0][wid] = sw;
-            red[1][wid] = sw2;
-            red[2][wid] = swa;
-            redm[wid] = mw;
-        }
-        __syncthreads();
-        if (threadIdx.x < 3) {
-            double t = 0.0;
-            for (int k = 0; k < kCountThreads / 32; ++k) t += red[threadIdx.x][k];
-            if (t != 0.0) atomicAdd(wsums + 4 * item + threadIdx.x, t);
-        } else if (threadIdx.x == 3) {
-            float m = 0.0f;
-            for (int k = 0; k < kCountThreads / 32; ++k) m = fmaxf(m, redm[k]);
-            atomicMax(wmax + item, __float_as_uint(m));
-        }
-    } else if (blockIdx.x == 0 && threadIdx.x < 3) {
-        atomicAdd(wsums + 4 * item + threadIdx.x, (double)(end - beg));   // exact below 2^53
-        if (threadIdx.x == 0) atomicMax(wmax + item, __float_as_uint(1.0f));
-    }
+    flush_wsums(sw, sw2, swa, mw, WEIGHTED, item, end - beg, wsums, wmax);
 }
 
 template <int DT>
@@ -611,6 +628,136 @@ k_paint_tiles(const float4 *__restrict__ sorted, const uint32_t *__restrict__ of
     }
 }
 
+// ---- direct atomic paint (the variant without a sort) ----
+// Per object: the same wrapped cell coordinate as the sort path, cell
+// c0 = floor(s) and offset u = (s - c0) + e along each axis; every deposit
+// round(w 2^S W) is added with a 64-bit global atomic (RED) into a dense
+// N^3 int64 accumulator per mesh.  Integer adds keep the accumulator
+// independent of object order.  The accumulator is converted and cleared by
+// k_acc_to_mesh.
+template <int P>
+__device__ __forceinline__ void deposit_global(unsigned long long *__restrict__ acc, int N,
+                                               const int *c0, const float *u, float sh, float ws) {
+    int bx, by, bz;
+    float wx[P], wy[P], wz[P];
+    spline_weights<P>(u[0] + sh, bx, wx);
+    spline_weights<P>(u[1] + sh, by, wy);
+    spline_weights<P>(u[2] + sh, bz, wz);
+    int cz[P];
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+        int v = c0[2] + bz + c;
+        v = v < 0 ? v + N : (v >= N ? v - N : v);
+        cz[c] = v;
+    }
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+        int cx = c0[0] + bx + a;
+        cx = cx < 0 ? cx + N : (cx >= N ? cx - N : cx);
+        const float vx = ws * wx[a];
+#pragma unroll
+        for (int b = 0; b < P; ++b) {
+            int cy = c0[1] + by + b;
+            cy = cy < 0 ? cy + N : (cy >= N ? cy - N : cy);
+            const float vxy = vx * wy[b];
+            unsigned long long *row = acc + ((long long)cx * N + cy) * N;
+#pragma unroll
+            for (int c = 0; c < P; ++c) {
+                // round(v) in one FMA when 0 <= round(v) < 2^22, else the
+                // rounded product converted to int64
+                const float t = fmaf(vxy, wz[c], 8388608.0f);
+                long long q;
+                if (t >= 8388608.0f && t < 12582912.0f) q = (long long)(__float_as_uint(t) - 0x4B000000u);
+                else q = __float2ll_rn(vxy * wz[c]);
+                if (q) atomicAdd(row + cz[c], (unsigned long long)q);
+            }
+        }
+    }
+}
+
+template <int DT, int P, int NM>
+__global__ void __launch_bounds__(kCountThreads)
+k_paint_atomic(const void *__restrict__ pos, const float *__restrict__ w,
+               const int64_t *__restrict__ item_off, PaintGeom g, int S, bool weighted,
+               unsigned long long *__restrict__ acc, double *__restrict__ wsums,
+               unsigned *__restrict__ wmax) {
+    using R = typename PosReal<DT>::type;
+    const int item = blockIdx.y;
+    const int64_t beg = item_off[item], end = item_off[item + 1];
+    const long long n3 = (long long)g.N * g.N * g.N;
+    unsigned long long *ab = acc + (long long)item * NM * n3;
+    const float scale = ldexpf(1.0f, S);
+    double sw = 0.0, sw2 = 0.0, swa = 0.0;
+    float mw = 0.0f;
+    for (int64_t i = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const Obj<R> o = load_obj<DT>(pos, w, i, g);
+        int c0[3];
+        float u[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            c0[a] = min((int)floor(o.s[a]), g.N - 1);
+            u[a] = (float)(o.s[a] - (R)c0[a]) + o.e[a];
+        }
+        const float ws = o.w * scale;
+#pragma unroll
+        for (int m = 0; m < NM; ++m) deposit_global<P>(ab + m * n3, g.N, c0, u, m ? 0.5f : 0.0f, ws);
+        if (weighted) {
+            const double wd = (double)o.w;
+            sw += wd;
+            sw2 += wd * wd;
+            swa += fabs(wd);
+            mw = fmaxf(mw, fabsf(o.w));
+        }
+    }
+    flush_wsums(sw, sw2, swa, mw, weighted, item, end - beg, wsums, wmax);
+}
+
+template <typename M>
+__device__ __forceinline__ M acc_value(unsigned long long q, float inv_scale);
+template <>
+__device__ __forceinline__ float acc_value<float>(unsigned long long q, float inv_scale) {
+    return ll_to_float_rn((long long)q) * inv_scale;
+}
+template <>
+__device__ __forceinline__ double acc_value<double>(unsigned long long q, float inv_scale) {
+    return __ll2double_rn((long long)q) * (double)inv_scale;
+}
+
+// Dense int64 accumulators (nitems x nm x N^3, z fastest) -> the r2c padded
+// mesh layout, two cells per thread; each accumulator pair is cleared after
+// it is read so the next paint starts from zero.
+template <typename M>
+__global__ void __launch_bounds__(256)
+k_acc_to_mesh(ulonglong2 *__restrict__ acc, long long npairs, int N, int nm, float inv_scale,
+              M *__restrict__ mesh, long long item_stride, long long mesh_stride, int accumulate) {
+    using M2 = typename std::conditional<sizeof(M) == 4, float2, double2>::type;
+    const long long n3 = (long long)N * N * N;
+    const long long pitch = 2LL * (N / 2 + 1);
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < npairs;
+         j += (long long)gridDim.x * blockDim.x) {
+        const long long cell = 2 * j;
+        const long long im = cell / n3;
+        const long long r = cell - im * n3;
+        const long long row = r / N;
+        const int cz = (int)(r - row * N);
+        const long long item = im / nm;
+        const int m = (int)(im - item * nm);
+        const ulonglong2 q = acc[j];
+        acc[j] = make_ulonglong2(0ull, 0ull);
+        M *dst = mesh + item * item_stride + m * mesh_stride + row * pitch + cz;
+        M2 v;
+        v.x = acc_value<M>(q.x, inv_scale);
+        v.y = acc_value<M>(q.y, inv_scale);
+        if (accumulate) {
+            const M2 o = *reinterpret_cast<const M2 *>(dst);
+            v.x += o.x;
+            v.y += o.y;
+        }
+        *reinterpret_cast<M2 *>(dst) = v;
+    }
+}
+
 // ---- fused compensate + interlace + bin ----
 template <typename C>
 __device__ __forceinline__ C cmul(C a, C b) {
@@ -984,6 +1131,29 @@ cudaError_t launch_sort_scatter(const void *pos, int dtype, const float *w, cons
     return cudaGetLastError();
 }
 
+// Small host arrays travel as kernel parameters (copied at launch, so the
+// host may reuse its array at once and a captured graph keeps the values).
+struct I64Chunk {
+    int64_t v[kUploadChunk];
+};
+
+__global__ void k_upload_i64(int64_t *__restrict__ dst, I64Chunk c, int n) {
+    if ((int)threadIdx.x < n) dst[threadIdx.x] = c.v[threadIdx.x];
+}
+
+cudaError_t launch_upload_i64(int64_t *dst, const int64_t *src, int n, int *launches, cudaStream_t st) {
+    for (int b = 0; b < n; b += kUploadChunk) {
+        const int m = n - b < kUploadChunk ? n - b : kUploadChunk;
+        I64Chunk c;
+        for (int k = 0; k < m; ++k) c.v[k] = src[b + k];
+        k_upload_i64<<<1, kUploadChunk, 0, st>>>(dst + b, c, m);
+        *launches += 1;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 size_t scan_tmp_elems(int64_t n) {
     size_t t = 0;
     while (n > 1) {
@@ -1058,6 +1228,71 @@ cudaError_t launch_paint_tiles(const float4 *sorted, const uint32_t *off, int ni
     PK_PAINT_CASE(4)
 #undef PK_PAINT_CASE
     return cudaErrorInvalidValue;
+}
+
+template <int DT, int P, int NM>
+static cudaError_t atomic_inst(const void *pos, const float *w, const int64_t *item_off, int nitems,
+                               int64_t max_n, const PaintGeom &g, int S, bool weighted,
+                               unsigned long long *acc, double *wsums, unsigned *wmax, cudaStream_t st) {
+    dim3 grid(grid_for(max_n, kCountThreads, 1u << 20), nitems);
+    k_paint_atomic<DT, P, NM><<<grid, kCountThreads, 0, st>>>(pos, w, item_off, g, S, weighted, acc,
+                                                             wsums, wmax);
+    return cudaGetLastError();
+}
+
+template <int DT>
+static cudaError_t atomic_dispatch(const void *pos, const float *w, const int64_t *item_off, int nitems,
+                                   int64_t max_n, const PaintGeom &g, int window, int nmesh, int S,
+                                   bool weighted, unsigned long long *acc, double *wsums, unsigned *wmax,
+                                   cudaStream_t st) {
+#define PK_ATOMIC_CASE(P)                                                                              \
+    if (window == P)                                                                                   \
+        return nmesh == 2 ? atomic_inst<DT, P, 2>(pos, w, item_off, nitems, max_n, g, S, weighted, acc, \
+                                                  wsums, wmax, st)                                    \
+                          : atomic_inst<DT, P, 1>(pos, w, item_off, nitems, max_n, g, S, weighted, acc, \
+                                                  wsums, wmax, st);
+    PK_ATOMIC_CASE(2)
+    PK_ATOMIC_CASE(3)
+    PK_ATOMIC_CASE(4)
+#undef PK_ATOMIC_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_paint_atomic(const void *pos, int dtype, const float *w, const int64_t *item_off,
+                                int nitems, int64_t max_n, const PaintGeom &g, int window, int nmesh,
+                                int S, unsigned long long *acc, double *wsums, unsigned *wmax,
+                                cudaStream_t st) {
+    const bool weighted = w != nullptr || dtype == PK_F32X4;
+    switch (dtype) {
+    case PK_F32:
+        return atomic_dispatch<PK_F32>(pos, w, item_off, nitems, max_n, g, window, nmesh, S, weighted, acc,
+                                       wsums, wmax, st);
+    case PK_F64:
+        return atomic_dispatch<PK_F64>(pos, w, item_off, nitems, max_n, g, window, nmesh, S, weighted, acc,
+                                       wsums, wmax, st);
+    default:
+        return atomic_dispatch<PK_F32X4>(pos, w, item_off, nitems, max_n, g, window, nmesh, S, weighted,
+                                         acc, wsums, wmax, st);
+    }
+}
+
+cudaError_t launch_acc_to_mesh(unsigned long long *acc, int nitems, int nmesh, int N, int S, int f64,
+                               void *mesh, long long item_stride, long long mesh_stride, int accumulate,
+                               int nsm, cudaStream_t st) {
+    const long long npairs = (long long)nitems * nmesh * N * N * N / 2;
+    if (npairs <= 0) return cudaSuccess;
+    const unsigned grid = grid_for(npairs, 256, (unsigned)(nsm > 0 ? nsm * 8 : 1024));
+    const float inv_scale = ldexpf(1.0f, -S);
+    ulonglong2 *a2 = reinterpret_cast<ulonglong2 *>(acc);
+    if (f64)
+        k_acc_to_mesh<double><<<grid, 256, 0, st>>>(a2, npairs, N, nmesh, inv_scale,
+                                                    reinterpret_cast<double *>(mesh), item_stride,
+                                                    mesh_stride, accumulate);
+    else
+        k_acc_to_mesh<float><<<grid, 256, 0, st>>>(a2, npairs, N, nmesh, inv_scale,
+                                                   reinterpret_cast<float *>(mesh), item_stride,
+                                                   mesh_stride, accumulate);
+    return cudaGetLastError();
 }
 
 size_t bin_smem_bytes(const BinGeom &g, int f64) {

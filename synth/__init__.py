@@ -143,3 +143,17 @@ def zeldovich_lattice(nside: int, box_size: float, seed: int, slope: float = -2.
         psis[a] = None
         del x
     return out
+
+
+def mock_set_specs(n_mocks: int, seed: int, n_lo: float = 2e5, n_hi: float = 4e6,
+                   meshes=(128, 192, 256), windows=("cic", "tsc")) -> list:
+    """Specs of a covariance mock set: per mock an object count log-uniform in
+    [n_lo, n_hi], a mesh size and a window drawn uniformly from the choices,
+    and the mock's own seed.  numpy PCG64 from `seed`."""
+    rng = np.random.default_rng(seed)
+    logn = rng.uniform(math.log(n_lo), math.log(n_hi), n_mocks)
+    ns = np.floor(np.exp(logn)).astype(np.int64)
+    nm = rng.choice(np.asarray(meshes), n_mocks)
+    wi = rng.integers(0, len(windows), n_mocks)
+    return [{"n": int(ns[i]), "nmesh": int(nm[i]), "window": windows[int(wi[i])],
+             "seed": int(seed) + 1 + i} for i in range(n_mocks)]

@@ -4,6 +4,7 @@ CUDA call."""
 import ctypes
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -53,7 +54,8 @@ def test_status_strings(pk):
     ("window", 5, "window"), ("dk", 0.0, "dk"), ("kmin", -0.1, "kmin"),
     ("nmu", -1, "nmu"), ("los_axis", 0, "los_axis"), ("precision", 3, "precision"),
     ("fixed_scale_log2", 50, "fixed_scale_log2"), ("batch", -2, "batch"),
-    ("poles_mask", 8, "poles_mask"),
+    ("poles_mask", 8, "poles_mask"), ("paint_variant", 2, "paint_variant"),
+    ("capacity", -1, "capacity"), ("capacity", 1 << 33, "capacity"),
 ])
 def test_plan_rejects_bad_config(pk, field, value, word):
     c = pk.make_config(1000.0, 64, "cic", dk=0.01)
@@ -79,3 +81,31 @@ def test_null_arguments(pk):
     assert lib.pk_compute(None) == pk.PK_EINVAL
     assert lib.pk_destroy(None) == pk.PK_OK
     assert lib.pk_last_error(None) == b""
+
+
+def _c_layout(tmp_path, struct, fields):
+    """sizeof and offsetof of a header struct, from a gcc-compiled probe."""
+    src = tmp_path / "layout.c"
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "pk.h"', "int main(void) {",
+             '  printf("%%zu\\n", sizeof(%s));' % struct]
+    lines += ['  printf("%%zu\\n", offsetof(%s, %s));' % (struct, f) for f in fields]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)]).decode().split()
+    return int(out[0]), [int(v) for v in out[1:]]
+
+
+@pytest.mark.parametrize("name", ["pk_config", "pk_result_view"])
+def test_ctypes_structs_match_the_header(pk, tmp_path, name):
+    cls = getattr(pk, name)
+    fields = [f for f, _ in cls._fields_]
+    size, offs = _c_layout(tmp_path, name, fields)
+    assert ctypes.sizeof(cls) == size
+    assert [getattr(cls, f).offset for f in fields] == offs
+
+
+def test_config_default_new_fields(pk):
+    c = pk.pk_config_default()
+    assert c.paint_variant == pk.PK_PAINT_SORT and c.capacity == 0 and c.tile == 0

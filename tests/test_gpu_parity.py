@@ -38,10 +38,10 @@ def torch_mod(pk):
 
 
 def run_gpu(pk, pos, weights, L, N, window, interlaced, dk, nmu=0, precision="f32",
-            compensated=True, stream=None, kmin=0.0, kmax=None, subtract_shot=True):
+            compensated=True, stream=None, kmin=0.0, kmax=None, subtract_shot=True, variant="sort"):
     cfg = pk.make_config(L, N, window, interlaced=interlaced, compensated=compensated, dk=dk,
                          nmu=nmu, precision=precision, kmin=kmin, kmax=kmax,
-                         subtract_shot=subtract_shot)
+                         subtract_shot=subtract_shot, paint_variant=variant)
     plan = pk.pk_plan(cfg, stream)
     try:
         pk.pk_paint(plan, pos, weights)
@@ -91,9 +91,10 @@ def compare(got, ref, tol, nmu=0):
 
 # ------------------------------------------------------------ paint step --
 
+@pytest.mark.parametrize("variant", ["sort", "atomic"])
 @pytest.mark.parametrize("window,interlaced", [("cic", False), ("tsc", True), ("pcs", True)])
 @pytest.mark.parametrize("N", [32, 40])
-def test_painted_mesh_matches_oracle_cell_by_cell(pk, oracle, window, interlaced, N):
+def test_painted_mesh_matches_oracle_cell_by_cell(pk, oracle, window, interlaced, N, variant):
     rng = np.random.default_rng(1000 + N)
     L = 250.0
     pos = rng.uniform(-0.5 * L, 1.5 * L, size=(20000, 3))
@@ -101,7 +102,8 @@ def test_painted_mesh_matches_oracle_cell_by_cell(pk, oracle, window, interlaced
                [L / N * 5, L / N * 7, L / N * 9], [L / N * 5.5, 0.5 * L / N, L],
                [3 * L, -2 * L, 0.25 * L], [1e-300, 1e-300, 1e-300]]
     w = rng.uniform(0.2, 2.0, 20000).astype(np.float32)
-    cfg = pk.make_config(L, N, window, interlaced=interlaced, dk=2 * math.pi / L * 2, precision="f64")
+    cfg = pk.make_config(L, N, window, interlaced=interlaced, dk=2 * math.pi / L * 2, precision="f64",
+                         paint_variant=variant)
     plan = pk.pk_plan(cfg)
     try:
         pk.pk_paint(plan, pos, w)
@@ -115,15 +117,16 @@ def test_painted_mesh_matches_oracle_cell_by_cell(pk, oracle, window, interlaced
         pk.pk_destroy(plan)
 
 
-def test_mesh_is_bit_identical_and_order_free(pk, torch_mod):
+@pytest.mark.parametrize("variant", ["sort", "atomic"])
+def test_mesh_is_bit_identical_and_order_free(pk, torch_mod, variant):
     """int64 fixed-point paint: the same catalog, painted twice and painted in
-    a shuffled order, gives byte-identical meshes."""
+    a shuffled order, gives byte-identical meshes (both paint variants)."""
     torch = torch_mod
     import synth
     L, N = 1000.0, 64
     pos = synth.lognormal_catalog(300000, L, N, synth.seed_for(2, 7), device="cuda")
     perm = torch.randperm(pos.shape[0], device="cuda", generator=torch.Generator("cuda").manual_seed(3))
-    cfg = pk.make_config(L, N, "tsc", interlaced=True, dk=0.02)
+    cfg = pk.make_config(L, N, "tsc", interlaced=True, dk=0.02, paint_variant=variant)
     plan = pk.pk_plan(cfg)
     try:
         meshes = []
@@ -157,7 +160,8 @@ def test_tiny_uniform_cic_both_precisions_host_and_device(pk, oracle, torch_mod)
 @pytest.mark.parametrize("window", ["cic", "tsc", "pcs"])
 @pytest.mark.parametrize("interlaced", [False, True])
 @pytest.mark.parametrize("precision", ["f32", "f64"])
-def test_window_interlace_precision_matrix(pk, oracle, torch_mod, window, interlaced, precision):
+@pytest.mark.parametrize("variant", ["sort", "atomic"])
+def test_window_interlace_precision_matrix(pk, oracle, torch_mod, window, interlaced, precision, variant):
     import synth
     L, N = 800.0, 48
     pos = synth.lognormal_catalog(60000, L, N, synth.seed_for(2, 11), device="cuda",
@@ -166,7 +170,7 @@ def test_window_interlace_precision_matrix(pk, oracle, torch_mod, window, interl
          + 0.5).float()
     dk = 1.5 * 2 * math.pi / L
     ref = run_oracle(oracle, pos, w, L, N, window, interlaced, dk, nmu=10)
-    got = run_gpu(pk, pos, w, L, N, window, interlaced, dk, nmu=10, precision=precision)
+    got = run_gpu(pk, pos, w, L, N, window, interlaced, dk, nmu=10, precision=precision, variant=variant)
     compare(got, ref, TOL[precision], nmu=10)
 
 
@@ -185,6 +189,20 @@ def test_ragged_and_small_tiles(pk, oracle, N, tile):
         compare(pk.pk_result(plan), ref, TOL["f64"], nmu=4)
     finally:
         pk.pk_destroy(plan)
+
+
+@pytest.mark.parametrize("N", [4, 6, 36])
+def test_atomic_variant_small_and_ragged_meshes(pk, oracle, N):
+    """The atomic variant wraps each deposit itself: windows wider than half
+    the mesh (PCS interlaced reaches 5 cells on N = 4) and N not a multiple
+    of 4."""
+    rng = np.random.default_rng(300 + N)
+    L = 100.0
+    pos = rng.uniform(-L, 2 * L, size=(5000, 3))
+    dk = 2 * math.pi / L
+    ref = run_oracle(oracle, pos, None, L, N, "pcs", True, dk, nmu=4)
+    got = run_gpu(pk, pos, None, L, N, "pcs", True, dk, nmu=4, precision="f64", variant="atomic")
+    compare(got, ref, TOL["f64"], nmu=4)
 
 
 def test_kmin_kmax_and_unsubtracted(pk, oracle):
@@ -223,18 +241,20 @@ def test_empty_catalog_gives_nan_not_a_crash(pk):
         pk.pk_destroy(plan)
 
 
-def test_single_object_and_one_dense_cell(pk, oracle):
+@pytest.mark.parametrize("variant", ["sort", "atomic"])
+def test_single_object_and_one_dense_cell(pk, oracle, variant):
     L, N = 64.0, 16
     dk = 2 * math.pi / L
     one = np.array([[12.3, 45.6, 63.999]])
-    compare(run_gpu(pk, one, None, L, N, "pcs", True, dk, precision="f64"),
+    compare(run_gpu(pk, one, None, L, N, "pcs", True, dk, precision="f64", variant=variant),
             run_oracle(oracle, one, None, L, N, "pcs", True, dk), TOL["f64"])
     dense = np.tile(np.array([[20.01, 20.02, 20.03]]), (200000, 1))
-    compare(run_gpu(pk, dense, None, L, N, "tsc", True, dk, precision="f64"),
+    compare(run_gpu(pk, dense, None, L, N, "tsc", True, dk, precision="f64", variant=variant),
             run_oracle(oracle, dense, None, L, N, "tsc", True, dk), TOL["f64"])
 
 
-def test_batch_equals_single(pk, torch_mod):
+@pytest.mark.parametrize("variant", ["sort", "atomic"])
+def test_batch_equals_single(pk, torch_mod, variant):
     import synth
     L, N = 500.0, 32
     sizes = [1000, 25000, 0, 7000]
@@ -242,7 +262,7 @@ def test_batch_equals_single(pk, torch_mod):
             for k, n in enumerate(sizes)]
     allpos = torch_mod.cat(cats).contiguous()
     off = np.concatenate([[0], np.cumsum(sizes)])
-    cfg = pk.make_config(L, N, "tsc", dk=2 * math.pi / L, nmu=4, batch=len(sizes))
+    cfg = pk.make_config(L, N, "tsc", dk=2 * math.pi / L, nmu=4, batch=len(sizes), paint_variant=variant)
     plan = pk.pk_plan(cfg)
     try:
         pk.pk_paint_many(plan, allpos, off)
@@ -254,7 +274,8 @@ def test_batch_equals_single(pk, torch_mod):
         if n == 0:
             assert np.all(np.isnan(batched[k]["power"]))
             continue
-        single = run_gpu(pk, cats[k].contiguous(), None, L, N, "tsc", False, 2 * math.pi / L, nmu=4)
+        single = run_gpu(pk, cats[k].contiguous(), None, L, N, "tsc", False, 2 * math.pi / L, nmu=4,
+                         variant=variant)
         ok = single["modes"] > 0
         raw = single["power"] + single["shot_noise"]          # pre-subtraction power
         assert np.all(np.abs(batched[k]["power"] - single["power"])[ok] <= 1e-6 * raw[ok])
@@ -264,11 +285,12 @@ def test_batch_equals_single(pk, torch_mod):
         assert np.all(np.isnan(batched[k]["power2d"][~ok2]))
 
 
-def test_accumulate_matches_single_paint(pk):
+@pytest.mark.parametrize("variant", ["sort", "atomic"])
+def test_accumulate_matches_single_paint(pk, variant):
     rng = np.random.default_rng(5)
     L, N = 200.0, 32
     pos = rng.uniform(0, L, size=(40000, 3)).astype(np.float32)
-    cfg = pk.make_config(L, N, "tsc", interlaced=True, dk=2 * math.pi / L)
+    cfg = pk.make_config(L, N, "tsc", interlaced=True, dk=2 * math.pi / L, paint_variant=variant)
     plan = pk.pk_plan(cfg)
     try:
         pk.pk_paint(plan, pos)
@@ -313,8 +335,9 @@ def test_call_order_errors(pk):
         pk.pk_destroy(plan)
 
 
-def test_overflow_headroom_reported(pk):
-    cfg = pk.make_config(100.0, 16, "cic", dk=0.2, fixed_scale_log2=40)
+@pytest.mark.parametrize("variant", ["sort", "atomic"])
+def test_overflow_headroom_reported(pk, variant):
+    cfg = pk.make_config(100.0, 16, "cic", dk=0.2, fixed_scale_log2=40, paint_variant=variant)
     plan = pk.pk_plan(cfg)
     try:
         pos = np.random.default_rng(2).uniform(0, 100, (10, 3))
