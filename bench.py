@@ -418,7 +418,8 @@ def measure_serving(pk, torch, world, rank, nreq, rate=200.0):
     arr = serve.poisson_arrivals(nreq, rate, synth.seed_for(5, 3 + 1000 * rank))
 
     def reqs(times):
-        return [serve.Request(i, c, float(t)) for i, (c, t) in enumerate(zip(cats, times))]
+        return [serve.Request(i, c, float(t), tag="large" if large[i] else "pool")
+                for i, (c, t) in enumerate(zip(cats, times))]
 
     out = {}
     warm = reqs(np.zeros(nreq))[: min(nreq, 64)] + [serve.Request(-1, big, 0.0)]

@@ -42,8 +42,12 @@ struct pk_plan_s {
     double kF = 0.0;
 
     void *mesh = nullptr;
-    cufftHandle fft = 0;
-    bool fft_made = false;
+    // cuFFT plans over 2^k catalogs (k = 0, 1, ...) and over the whole batch,
+    // so a compute of n < batch catalogs transforms only their meshes; one
+    // shared work area.
+    std::vector<int> fft_items;
+    std::vector<cufftHandle> fft;
+    void *fft_work = nullptr;
 
     uint32_t *d_count = nullptr;     // objects per (tile, class) key
     uint32_t *d_off = nullptr;       // exclusive scan of d_count (+ total)
@@ -119,11 +123,11 @@ cudaError_t dev_alloc(T **ptr, size_t bytes) {
 void free_plan(pk_plan_s *p) {
     if (!p) return;
     cudaStreamSynchronize(p->st);
-    if (p->fft_made) cufftDestroy(p->fft);
+    for (cufftHandle h : p->fft) cufftDestroy(h);
     void *dev[] = {p->mesh, p->d_count, p->d_off, p->d_scan_tmp, p->d_rank, p->d_sorted,
                    p->d_stage, p->d_item_off, p->d_wsums, p->d_wmax, p->d_cw, p->d_ph,
                    p->d_kedge, p->d_partial, p->d_sums2, p->d_res, p->d_modes1d, p->d_modes2d,
-                   p->d_err, p->d_acc};
+                   p->d_err, p->d_acc, p->fft_work};
     for (void *d : dev)
         if (d) cudaFree(d);
     if (p->h_res) cudaFreeHost(p->h_res);
@@ -465,17 +469,26 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
         PK_CUDA(P, cudaMemcpy(P->d_modes1d, P->modes1d.data(), 8 * nk, cudaMemcpyHostToDevice));
     }
 
-    // ---- cuFFT: batched in-place r2c over every mesh of the plan ----
+    // ---- cuFFT: batched in-place r2c, plans over 1, 2, 4, ... catalogs and all B ----
     {
-        PK_CUFFT(P, cufftCreate(&P->fft));
-        P->fft_made = true;
+        for (int c = 1; c < P->B; c <<= 1) P->fft_items.push_back(c);
+        P->fft_items.push_back(P->B);
         long long n[3] = {P->N, P->N, P->N};
         long long inembed[3] = {P->N, P->N, 2LL * P->Nh};
         long long onembed[3] = {P->N, P->N, (long long)P->Nh};
-        size_t work = 0;
-        PK_CUFFT(P, cufftMakePlanMany64(P->fft, 3, n, inembed, 1, P->mesh_reals, onembed, 1,
-                                        P->mesh_reals / 2, P->f64 ? CUFFT_D2Z : CUFFT_R2C,
-                                        (long long)P->B * P->nm, &work));
+        size_t work_max = 0;
+        for (int c : P->fft_items) {
+            cufftHandle h;
+            PK_CUFFT(P, cufftCreate(&h));
+            P->fft.push_back(h);
+            PK_CUFFT(P, cufftSetAutoAllocation(h, 0));
+            size_t work = 0;
+            PK_CUFFT(P, cufftMakePlanMany64(h, 3, n, inembed, 1, P->mesh_reals, onembed, 1, P->mesh_reals / 2,
+                                            P->f64 ? CUFFT_D2Z : CUFFT_R2C, (long long)c * P->nm, &work));
+            work_max = std::max(work_max, work);
+        }
+        PK_CUDA(P, dev_alloc(&P->fft_work, work_max));
+        for (cufftHandle h : P->fft) PK_CUFFT(P, cufftSetWorkArea(h, P->fft_work));
     }
     return PK_OK;
 }
@@ -494,10 +507,12 @@ pk_status pk_plan(const pk_config *cfg, void *cuda_stream, pk_plan_t *out) {
         return s;
     }
     P->st = reinterpret_cast<cudaStream_t>(cuda_stream);
-    if (cufftSetStream(P->fft, P->st) != CUFFT_SUCCESS) {
-        g_plan_error = "cufftSetStream failed";
-        free_plan(P);
-        return PK_ECUFFT;
+    for (cufftHandle h : P->fft) {
+        if (cufftSetStream(h, P->st) != CUFFT_SUCCESS) {
+            g_plan_error = "cufftSetStream failed";
+            free_plan(P);
+            return PK_ECUFFT;
+        }
     }
     *out = P;
     return PK_OK;
@@ -655,12 +670,27 @@ pk_status pk_compute(pk_plan_t P) {
     const int cap = capturing(st);
     const int tm = P->timing && !cap;
     if (tm) PK_CUDA(P, cudaEventRecord(P->tev[3], st));
-    if (P->f64) {
-        cufftDoubleReal *r = reinterpret_cast<cufftDoubleReal *>(P->mesh);
-        PK_CUFFT(P, cufftExecD2Z(P->fft, r, reinterpret_cast<cufftDoubleComplex *>(r)));
-    } else {
-        cufftReal *r = reinterpret_cast<cufftReal *>(P->mesh);
-        PK_CUFFT(P, cufftExecR2C(P->fft, r, reinterpret_cast<cufftComplex *>(r)));
+    {
+        // the painted catalogs: the whole-batch plan, else the binary digits of
+        // the count (every power of two below B has a plan, and count < B)
+        const int nplans = (int)P->fft.size();
+        int left = P->npainted, at = 0;
+        for (int k = nplans - 1; k >= 0 && left > 0; --k) {
+            const int c = P->fft_items[k];
+            const bool whole = k == nplans - 1;
+            if (whole ? c != left : c > left) continue;
+            const size_t off = (size_t)at * P->nm * P->mesh_reals;
+            if (P->f64) {
+                cufftDoubleReal *r = reinterpret_cast<cufftDoubleReal *>(P->mesh) + off;
+                PK_CUFFT(P, cufftExecD2Z(P->fft[k], r, reinterpret_cast<cufftDoubleComplex *>(r)));
+            } else {
+                cufftReal *r = reinterpret_cast<cufftReal *>(P->mesh) + off;
+                PK_CUFFT(P, cufftExecR2C(P->fft[k], r, reinterpret_cast<cufftComplex *>(r)));
+            }
+            at += c;
+            left -= c;
+        }
+        if (left != 0) return fail(P, PK_ECUFFT, "internal: catalog count not covered by the FFT plans");
     }
     P->transformed = 1;
     if (tm) PK_CUDA(P, cudaEventRecord(P->tev[4], st));

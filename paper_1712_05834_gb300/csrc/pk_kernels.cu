@@ -499,6 +499,68 @@ __device__ __forceinline__ void deposit_any(const float4 *cand, uint32_t n, unsi
     else deposit_staged<P, 0>(cand, n, lo, hi, acc64, sp, T, sh);
 }
 
+// Both meshes of an interlaced pair in one sweep over the candidates (MODE 2
+// only: the hi words of the split are free and hold mesh 1).
+template <int P>
+__device__ __forceinline__ void deposit_both(const float4 *cand, uint32_t n, unsigned *lo0, unsigned *lo1,
+                                             const Split &sp, int T) {
+    for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const float4 v = cand[j];
+        deposit<P, 2>(lo0, nullptr, nullptr, sp, T, v.x, v.y, v.z, v.w);
+        deposit<P, 2>(lo1, nullptr, nullptr, sp, T, v.x + 0.5f, v.y + 0.5f, v.z + 0.5f, v.w);
+    }
+}
+
+// Write one tile's cells to the mesh (r2c layout, rows of T cells along z at
+// the given pitch).  Sources: lo alone (no split), lo + hi (split), or acc64
+// (64-bit cells).  Even T: two cells per thread with 8- (FP32) or 16-byte
+// (FP64) stores; the row pitch and tile origin are even, so they are aligned.
+template <typename M, int TC>
+__device__ __forceinline__ void flush_tile(const unsigned *lo, const unsigned *hi, const unsigned long long *acc64,
+                                           const Split &sp, float inv_scale, M *__restrict__ mb, int T, int N,
+                                           long long pitch, int accumulate) {
+    using M2 = typename std::conditional<sizeof(M) == 4, float2, double2>::type;
+    if ((T & 1) == 0) {
+        const int hT = T >> 1;
+        const int npairs = T * T * hT;
+        for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+            const int r = TC > 0 ? p / (TC / 2) : p / hT;           // row = cx T + cy
+            const int cz = 2 * (p - r * hT);
+            const int cx = TC > 0 ? r / TC : r / T;
+            const int cy = r - cx * T;
+            const int c = r * T + cz;
+            M2 v;
+            if (acc64) {
+                v.x = cell_value<M>(0u, 0u, acc64[c], sp, inv_scale);
+                v.y = cell_value<M>(0u, 0u, acc64[c + 1], sp, inv_scale);
+            } else {
+                const uint2 l2 = *reinterpret_cast<const uint2 *>(lo + c);
+                const uint2 h2 = hi ? *reinterpret_cast<const uint2 *>(hi + c) : make_uint2(0u, 0u);
+                v.x = cell_value<M>(l2.x, h2.x, 0ull, sp, inv_scale);
+                v.y = cell_value<M>(l2.y, h2.y, 0ull, sp, inv_scale);
+            }
+            M2 *dst = reinterpret_cast<M2 *>(mb + ((long long)cx * N + cy) * pitch + cz);
+            if (accumulate) {
+                const M2 o = *dst;
+                v.x += o.x;
+                v.y += o.y;
+            }
+            *dst = v;
+        }
+    } else {
+        const int n = T * T * T;
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            const int r = c / T, cz = c - r * T;
+            const int cx = r / T, cy = r - cx * T;
+            const M val = acc64 ? cell_value<M>(0u, 0u, acc64[c], sp, inv_scale)
+                                : cell_value<M>(lo[c], hi ? hi[c] : 0u, 0ull, sp, inv_scale);
+            M *dst = mb + ((long long)cx * N + cy) * pitch + cz;
+            if (accumulate) *dst += val;
+            else *dst = val;
+        }
+    }
+}
+
 // TC > 0: the tile edge is the compile-time constant TC (index math in shifts).
 template <int P, int NM, typename M, int TC>
 __global__ void __launch_bounds__(kPaintThreads)
@@ -588,8 +650,13 @@ k_paint_tiles(const float4 *__restrict__ sorted, const uint32_t *__restrict__ of
     const long long pitch = 2LL * (g.N / 2 + 1);
     M *base = mesh + item * item_stride;
 
+    // With no split needed (unit weights, sparse tile) both meshes of an
+    // interlaced pair are painted in one pass: mesh 0 into lo, mesh 1 into hi.
+    const bool both = NM == 2 && sp.fast == 2;
+    const int passes = both ? 1 : NM;
+    const long long tile_off = ((long long)tx * T * g.N + (long long)ty * T) * pitch + (long long)tz * T;
 #pragma unroll 1
-    for (int m = 0; m < NM; ++m) {
+    for (int m = 0; m < passes; ++m) {
         {
             uint4 *z4 = reinterpret_cast<uint4 *>(smu);
             const int n4 = (2 * T3) / 4;
@@ -599,30 +666,26 @@ k_paint_tiles(const float4 *__restrict__ sorted, const uint32_t *__restrict__ of
         __syncthreads();
         const float sh = m ? 0.5f : 0.0f;
         if (staged_once) {
-            deposit_any<P>(cand, total, lo, hi, acc64, sp, T, sh);
+            if (both) deposit_both<P>(cand, total, lo, hi, sp, T);
+            else deposit_any<P>(cand, total, lo, hi, acc64, sp, T, sh);
         } else {
             for (uint32_t k0 = 0; k0 < total; k0 += kStage) {     // dense tile: batches
                 const uint32_t n = min((uint32_t)kStage, total - k0);
                 __syncthreads();                                  // previous batch consumed
                 stage_candidates(sorted, s_beg, s_pre, s_shift, k0, n, scale, cand);
                 __syncthreads();
-                deposit_any<P>(cand, n, lo, hi, acc64, sp, T, sh);
+                if (both) deposit_both<P>(cand, n, lo, hi, sp, T);
+                else deposit_any<P>(cand, n, lo, hi, acc64, sp, T, sh);
             }
         }
         __syncthreads();
-        M *mb = base + m * mesh_stride + ((long long)tx * T * g.N + (long long)ty * T) * pitch +
-                (long long)tz * T;
-        // rows of T cells along z: thread -> (row, cz); rows (cx, cy) advance together
-        const int rows_per_pass = blockDim.x / T;
-        const int cz = threadIdx.x % T;
-        for (int r = threadIdx.x / T; r < T * T && threadIdx.x < rows_per_pass * T; r += rows_per_pass) {
-            const int cx = r / T, cy = r - cx * T;
-            const int c = r * T + cz;
-            const long long idx = ((long long)cx * g.N + cy) * pitch + cz;
-            const M val = sp.fast ? cell_value<M>(lo[c], sp.fast == 2 ? 0u : hi[c], 0ull, sp, inv_scale)
-                                  : cell_value<M>(0u, 0u, acc64[c], sp, inv_scale);
-            if (accumulate) mb[idx] += val;
-            else mb[idx] = val;
+        if (both) {
+            flush_tile<M, TC>(lo, nullptr, nullptr, sp, inv_scale, base + tile_off, T, g.N, pitch, accumulate);
+            flush_tile<M, TC>(hi, nullptr, nullptr, sp, inv_scale, base + mesh_stride + tile_off, T, g.N, pitch,
+                              accumulate);
+        } else {
+            flush_tile<M, TC>(sp.fast ? lo : nullptr, sp.fast == 1 ? hi : nullptr, sp.fast ? nullptr : acc64, sp,
+                              inv_scale, base + m * mesh_stride + tile_off, T, g.N, pitch, accumulate);
         }
         __syncthreads();
     }

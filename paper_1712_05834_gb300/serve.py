@@ -49,6 +49,7 @@ class Request:
     result: dict | None = None
     t_done: float = float("nan")
     batch_size: int = 0
+    tag: str = ""
 
     @property
     def latency(self) -> float:
@@ -324,10 +325,19 @@ def poisson_arrivals(n: int, rate: float, seed: int) -> np.ndarray:
 
 
 def latency_summary(reqs) -> dict:
+    """p50 / p99 / mean / max latency (ms), served P(k)/s over the run, mean
+    batch size; per tag as well when the requests carry tags."""
     lat = np.array([r.latency for r in reqs]) * 1e3
     t_end = max(r.t_done for r in reqs)
     t_begin = min(r.arrival for r in reqs)
-    return {"requests": len(reqs), "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-            "max_ms": float(lat.max()), "pk_per_s": len(reqs) / max(t_end - t_begin, 1e-9),
-            "mean_batch": float(np.mean([r.batch_size for r in reqs]))}
+    out = {"requests": len(reqs), "p50_ms": float(np.percentile(lat, 50)),
+           "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+           "max_ms": float(lat.max()), "pk_per_s": len(reqs) / max(t_end - t_begin, 1e-9),
+           "mean_batch": float(np.mean([r.batch_size for r in reqs]))}
+    tags = sorted({r.tag for r in reqs if r.tag})
+    for t in tags:
+        lt = np.array([r.latency for r in reqs if r.tag == t]) * 1e3
+        out["by_tag"] = out.get("by_tag", {})
+        out["by_tag"][t] = {"requests": int(lt.size), "p50_ms": float(np.percentile(lt, 50)),
+                            "p99_ms": float(np.percentile(lt, 99)), "max_ms": float(lt.max())}
+    return out

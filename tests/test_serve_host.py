@@ -40,3 +40,15 @@ def test_latency_summary():
     assert s["max_ms"] == pytest.approx(100.0)
     assert s["pk_per_s"] == pytest.approx(100 / (0.99 + 0.1))
     assert s["mean_batch"] == pytest.approx(np.mean([1 + i % 3 for i in range(100)]))
+
+
+def test_latency_summary_by_tag():
+    reqs = []
+    for i in range(40):
+        r = serve.Request(i, None, arrival=0.0, tag="large" if i % 10 == 0 else "pool")
+        r.t_done = 0.1 if r.tag == "large" else 0.001
+        reqs.append(r)
+    s = serve.latency_summary(reqs)
+    assert s["by_tag"]["large"]["requests"] == 4 and s["by_tag"]["pool"]["requests"] == 36
+    assert s["by_tag"]["large"]["p50_ms"] == pytest.approx(100.0)
+    assert s["by_tag"]["pool"]["p99_ms"] == pytest.approx(1.0)
