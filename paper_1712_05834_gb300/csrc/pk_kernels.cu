@@ -53,14 +53,14 @@ namespace {
 constexpr int kCountThreads = 256;
 constexpr int kPaintThreads = 256;
 constexpr int kBinThreads = 256;
-constexpr int kBinVec = 8;            // consecutive modes per thread
+constexpr int kBinVec = 4;            // consecutive modes per thread
 constexpr int kScanThreads = 1024;
 constexpr int kScanPer = 4;           // elements per thread in a scan block
 constexpr int kScanTile = kScanThreads * kScanPer;
 constexpr int kClasses = 27;          // boundary classes per tile
 constexpr int kSegments = 75;         // (neighbour, class range) segments per tile
 constexpr int kReduceChunk = 32;      // per-CTA histograms summed per reduce block
-constexpr int kStage = 512;           // candidates staged in shared memory per batch
+constexpr int kStage = 256;           // candidates staged in shared memory per batch (small: 6 CTAs / SM)
 constexpr int kUploadChunk = 256;     // int64 values per parameter upload (2 KB)
 
 __device__ __forceinline__ int wrapmod(int a, int n) {
@@ -370,7 +370,7 @@ struct Split {
 // weights): one FMA, one subtract, one 32-bit shared atomic per cell.
 // MODE 1: as 2, with a split into hi * 2^B + lo for the rare large or
 // negative deposit.  MODE 0: 64-bit shared atomics (dense tiles).
-template <int P, int MODE>
+template <int P, int MODE, int TC = 0>
 __device__ __forceinline__ void deposit(unsigned *lo, unsigned *hi, unsigned long long *acc64,
                                         const Split &sp, int T, float x, float y, float z, float ws) {
     int bx, by, bz;
@@ -482,32 +482,32 @@ __device__ __forceinline__ void stage_candidates(const float4 *__restrict__ sort
     }
 }
 
-template <int P, int MODE>
+template <int P, int MODE, int TC>
 __device__ __forceinline__ void deposit_staged(const float4 *cand, uint32_t n, unsigned *lo, unsigned *hi,
                                                unsigned long long *acc64, const Split &sp, int T, float sh) {
     for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
         const float4 v = cand[j];
-        deposit<P, MODE>(lo, hi, acc64, sp, T, v.x + sh, v.y + sh, v.z + sh, v.w);
+        deposit<P, MODE, TC>(lo, hi, acc64, sp, T, v.x + sh, v.y + sh, v.z + sh, v.w);
     }
 }
 
-template <int P>
+template <int P, int TC>
 __device__ __forceinline__ void deposit_any(const float4 *cand, uint32_t n, unsigned *lo, unsigned *hi,
                                             unsigned long long *acc64, const Split &sp, int T, float sh) {
-    if (sp.fast == 2) deposit_staged<P, 2>(cand, n, lo, hi, acc64, sp, T, sh);
-    else if (sp.fast == 1) deposit_staged<P, 1>(cand, n, lo, hi, acc64, sp, T, sh);
-    else deposit_staged<P, 0>(cand, n, lo, hi, acc64, sp, T, sh);
+    if (sp.fast == 2) deposit_staged<P, 2, TC>(cand, n, lo, hi, acc64, sp, T, sh);
+    else if (sp.fast == 1) deposit_staged<P, 1, TC>(cand, n, lo, hi, acc64, sp, T, sh);
+    else deposit_staged<P, 0, TC>(cand, n, lo, hi, acc64, sp, T, sh);
 }
 
 // Both meshes of an interlaced pair in one sweep over the candidates (MODE 2
 // only: the hi words of the split are free and hold mesh 1).
-template <int P>
+template <int P, int TC>
 __device__ __forceinline__ void deposit_both(const float4 *cand, uint32_t n, unsigned *lo0, unsigned *lo1,
                                              const Split &sp, int T) {
     for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
         const float4 v = cand[j];
-        deposit<P, 2>(lo0, nullptr, nullptr, sp, T, v.x, v.y, v.z, v.w);
-        deposit<P, 2>(lo1, nullptr, nullptr, sp, T, v.x + 0.5f, v.y + 0.5f, v.z + 0.5f, v.w);
+        deposit<P, 2, TC>(lo0, nullptr, nullptr, sp, T, v.x, v.y, v.z, v.w);
+        deposit<P, 2, TC>(lo1, nullptr, nullptr, sp, T, v.x + 0.5f, v.y + 0.5f, v.z + 0.5f, v.w);
     }
 }
 
@@ -520,7 +520,42 @@ __device__ __forceinline__ void flush_tile(const unsigned *lo, const unsigned *h
                                            const Split &sp, float inv_scale, M *__restrict__ mb, int T, int N,
                                            long long pitch, int accumulate) {
     using M2 = typename std::conditional<sizeof(M) == 4, float2, double2>::type;
-    if ((T & 1) == 0) {
+    constexpr int kPlane = TC > 0 ? (TC / 2) * TC : 1;                 // cell pairs per x-plane
+    constexpr bool kFixed = TC > 0 && TC % 2 == 0 && kPaintThreads % kPlane == 0 &&
+                            TC % (kPaintThreads / kPlane) == 0;
+    if constexpr (kFixed) {
+        // each pass of the CTA covers whole x-planes: a thread keeps its
+        // (cy, cz) and steps cx by a fixed stride, in shared and global memory
+        constexpr int hT = TC > 0 ? TC / 2 : 1;
+        constexpr int planes = kFixed ? kPaintThreads / kPlane : 1;
+        const int t = threadIdx.x;
+        const int cz = 2 * (t % hT);
+        const int cy = (t / hT) % TC;
+        const int cx0 = t / (hT * TC);
+        int c = (cx0 * TC + cy) * TC + cz;
+        M *dst = mb + ((long long)cx0 * N + cy) * pitch + cz;
+        const long long gstep = (long long)planes * N * pitch;
+#pragma unroll 2
+        for (int k = 0; k < TC / planes; ++k, c += planes * TC * TC, dst += gstep) {
+            M2 v;
+            if (acc64) {
+                v.x = cell_value<M>(0u, 0u, acc64[c], sp, inv_scale);
+                v.y = cell_value<M>(0u, 0u, acc64[c + 1], sp, inv_scale);
+            } else {
+                const uint2 l2 = *reinterpret_cast<const uint2 *>(lo + c);
+                const uint2 h2 = hi ? *reinterpret_cast<const uint2 *>(hi + c) : make_uint2(0u, 0u);
+                v.x = cell_value<M>(l2.x, h2.x, 0ull, sp, inv_scale);
+                v.y = cell_value<M>(l2.y, h2.y, 0ull, sp, inv_scale);
+            }
+            M2 *d2 = reinterpret_cast<M2 *>(dst);
+            if (accumulate) {
+                const M2 o = *d2;
+                v.x += o.x;
+                v.y += o.y;
+            }
+            *d2 = v;
+        }
+    } else if ((T & 1) == 0) {
         const int hT = T >> 1;
         const int npairs = T * T * hT;
         for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
@@ -666,16 +701,16 @@ k_paint_tiles(const float4 *__restrict__ sorted, const uint32_t *__restrict__ of
         __syncthreads();
         const float sh = m ? 0.5f : 0.0f;
         if (staged_once) {
-            if (both) deposit_both<P>(cand, total, lo, hi, sp, T);
-            else deposit_any<P>(cand, total, lo, hi, acc64, sp, T, sh);
+            if (both) deposit_both<P, TC>(cand, total, lo, hi, sp, T);
+            else deposit_any<P, TC>(cand, total, lo, hi, acc64, sp, T, sh);
         } else {
             for (uint32_t k0 = 0; k0 < total; k0 += kStage) {     // dense tile: batches
                 const uint32_t n = min((uint32_t)kStage, total - k0);
                 __syncthreads();                                  // previous batch consumed
                 stage_candidates(sorted, s_beg, s_pre, s_shift, k0, n, scale, cand);
                 __syncthreads();
-                if (both) deposit_both<P>(cand, n, lo, hi, sp, T);
-                else deposit_any<P>(cand, n, lo, hi, acc64, sp, T, sh);
+                if (both) deposit_both<P, TC>(cand, n, lo, hi, sp, T);
+                else deposit_any<P, TC>(cand, n, lo, hi, acc64, sp, T, sh);
             }
         }
         __syncthreads();
