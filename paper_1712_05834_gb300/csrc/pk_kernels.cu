@@ -52,7 +52,7 @@ namespace {
 
 constexpr int kCountThreads = 256;
 constexpr int kPaintThreads = 256;
-constexpr int kBinThreads = 256;
+constexpr int kBinThreads = 512;
 constexpr int kBinVec = 4;            // consecutive modes per thread
 constexpr int kScanThreads = 1024;
 constexpr int kScanPer = 4;           // elements per thread in a scan block
