@@ -463,11 +463,18 @@ __device__ __forceinline__ int ceil_log2(unsigned x) {     // x >= 1
     return x <= 1u ? 0 : 32 - __clz(x - 1u);
 }
 
+// Neighbour offset (-1, 0, +1 per axis) of gather segment s: s = (ax * 5 + ay)
+// * 3 + az with ax, ay over the 5 (offset, class) pairs -- offset -1, three
+// classes at offset 0, offset +1 -- and az over the 3 z offsets.
+__device__ __forceinline__ int seg_dx(int s) { const int ax = s / 15; return ax == 0 ? -1 : (ax == 4 ? 1 : 0); }
+__device__ __forceinline__ int seg_dy(int s) { const int ay = (s / 3) % 5; return ay == 0 ? -1 : (ay == 4 ? 1 : 0); }
+__device__ __forceinline__ int seg_dz(int s) { return s % 3 - 1; }
+
 // Copy candidates [k0, k0 + n) of the tile into shared memory, already in this
 // tile's frame (segment shift added) and with the weight scaled by 2^S.
 __device__ __forceinline__ void stage_candidates(const float4 *__restrict__ sorted, const uint32_t *s_beg,
-                                                 const uint32_t *s_pre, const float (*s_shift)[3],
-                                                 uint32_t k0, uint32_t n, float scale, float4 *cand) {
+                                                 const uint32_t *s_pre, int T, uint32_t k0, uint32_t n,
+                                                 float scale, float4 *cand) {
     for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
         const uint32_t k = k0 + j;
         int lo_s = 0, hi_s = kSegments;               // s_pre[lo_s] <= k < s_pre[hi_s]
@@ -477,8 +484,8 @@ __device__ __forceinline__ void stage_candidates(const float4 *__restrict__ sort
             else hi_s = mid;
         }
         const float4 v = __ldg(sorted + s_beg[lo_s] + (k - s_pre[lo_s]));
-        cand[j] = make_float4(v.x + s_shift[lo_s][0], v.y + s_shift[lo_s][1], v.z + s_shift[lo_s][2],
-                              v.w * scale);
+        cand[j] = make_float4(v.x + (float)(seg_dx(lo_s) * T), v.y + (float)(seg_dy(lo_s) * T),
+                              v.z + (float)(seg_dz(lo_s) * T), v.w * scale);
     }
 }
 
@@ -605,7 +612,6 @@ k_paint_tiles(const float4 *__restrict__ sorted, const uint32_t *__restrict__ of
     extern __shared__ __align__(16) unsigned smu[];   // lo[T^3], hi[T^3] or acc64[T^3]; cand[kStage]
     __shared__ uint32_t s_beg[kSegments];
     __shared__ uint32_t s_pre[kSegments + 1];
-    __shared__ float s_shift[kSegments][3];
     const int T = TC > 0 ? TC : g.T, T3 = T * T * T;
     unsigned *lo = smu, *hi = smu + T3;
     unsigned long long *acc64 = reinterpret_cast<unsigned long long *>(smu);
@@ -636,9 +642,6 @@ k_paint_tiles(const float4 *__restrict__ sorted, const uint32_t *__restrict__ of
         const uint32_t b = off[kb + cz0], e = off[kb + cz1 + 1];
         s_beg[s] = b;
         s_pre[s + 1] = e - b;
-        s_shift[s][0] = (float)(dx * T);
-        s_shift[s][1] = (float)(dy * T);
-        s_shift[s][2] = (float)(dz * T);
     }
     __syncthreads();
     if (threadIdx.x < 32) {                          // warp scan of the 75 lengths
@@ -681,7 +684,7 @@ k_paint_tiles(const float4 *__restrict__ sorted, const uint32_t *__restrict__ of
     const float scale = ldexpf(1.0f, S);
     const float inv_scale = ldexpf(1.0f, -S);
     const bool staged_once = total <= (uint32_t)kStage;
-    if (staged_once) stage_candidates(sorted, s_beg, s_pre, s_shift, 0u, total, scale, cand);
+    if (staged_once) stage_candidates(sorted, s_beg, s_pre, T, 0u, total, scale, cand);
     const long long pitch = 2LL * (g.N / 2 + 1);
     M *base = mesh + item * item_stride;
 
@@ -707,7 +710,7 @@ k_paint_tiles(const float4 *__restrict__ sorted, const uint32_t *__restrict__ of
             for (uint32_t k0 = 0; k0 < total; k0 += kStage) {     // dense tile: batches
                 const uint32_t n = min((uint32_t)kStage, total - k0);
                 __syncthreads();                                  // previous batch consumed
-                stage_candidates(sorted, s_beg, s_pre, s_shift, k0, n, scale, cand);
+                stage_candidates(sorted, s_beg, s_pre, T, k0, n, scale, cand);
                 __syncthreads();
                 if (both) deposit_both<P, TC>(cand, n, lo, hi, sp, T);
                 else deposit_any<P, TC>(cand, n, lo, hi, acc64, sp, T, sh);
