@@ -27,6 +27,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pk_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "lognormal_oracle.c")]
 _LIB = os.path.join(_HERE, "_pk_oracle.so")
 _lib = None
 
@@ -36,11 +37,11 @@ WINDOW_ORDER = {"cic": 2, "tsc": 3, "pcs": 4}
 def build(force: bool = False) -> str:
     """Compile pk_oracle.c into oracle/_pk_oracle.so with gcc (FP64, no FMA
     contraction so the k-bin expression rounds exactly as written)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(f) for f in _SRCS):
         tmp = _LIB + ".%d.tmp" % os.getpid()
         subprocess.check_call([
-            "gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
-            "-fno-fast-math", "-fopenmp", _SRC, "-o", tmp, "-lm"])
+            "gcc", "-O2", "-std=gnu99", "-fPIC", "-shared", "-ffp-contract=off",
+            "-fno-fast-math", "-fopenmp"] + _SRCS + ["-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -64,6 +65,12 @@ def _load():
         lib.oracle_paint_block.restype = i
         lib.oracle_mode_counts.argtypes = [i, d, d, d, i, i, p, p]
         lib.oracle_mode_counts.restype = i
+        lib.oracle_philox4x64.argtypes = [p, p, p]
+        lib.oracle_philox4x64.restype = None
+        lib.oracle_white_noise.argtypes = [i, ctypes.c_uint64, p]
+        lib.oracle_white_noise.restype = i
+        lib.oracle_place.argtypes = [p, i, d, p, d, ctypes.c_uint64, i64, p]
+        lib.oracle_place.restype = i
         _lib = lib
     return _lib
 
@@ -215,3 +222,103 @@ def fft_power(pos, weights, box_size, nmesh, window="cic", interlaced=False,
     res["wsum"], res["w2sum"] = wsum, w2sum
     res["nk"], res["nmu"] = sums["nk"], sums["nmu"]
     return res
+
+
+# ------------------------------------------------------------------------
+# Log-normal mock generator (LogNormalCatalog of the paper's tests and
+# benchmarks, Sec. 3.2), FP64.  Random numbers: Philox4x64-10 (see
+# lognormal_oracle.c for the stream layout).
+# ------------------------------------------------------------------------
+
+def philox4x64(ctr, key):
+    """One Philox4x64-10 block: four 64-bit words."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint64).reshape(4))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint64).reshape(2))
+    out = np.zeros(4, np.uint64)
+    _load().oracle_philox4x64(_ptr(c), _ptr(k), _ptr(out))
+    return [int(v) for v in out]
+
+
+def white_noise(ng: int, seed: int):
+    """ng^3 unit Gaussians (Box-Muller on Philox words), C order, z fastest."""
+    out = np.zeros((ng, ng, ng), np.float64)
+    if _load().oracle_white_noise(int(ng), int(seed), _ptr(out)) != 0:
+        raise ValueError("oracle_white_noise: bad arguments")
+    return out
+
+
+def _k2_grid(ng: int, box_size: float):
+    kf = 2.0 * math.pi / box_size
+    f = np.fft.fftfreq(ng, 1.0 / ng) * kf
+    fz = np.fft.rfftfreq(ng, 1.0 / ng) * kf
+    return f[:, None, None], f[None, :, None], fz[None, None, :]
+
+
+def lognormal_amplitude(ng: int, box_size: float, slope: float, variance: float = 1.0) -> float:
+    """A with (1 / L^3) sum_{k != 0} A k^slope = variance over the full ng^3 grid."""
+    kf = 2.0 * math.pi / box_size
+    f = np.fft.fftfreq(ng, 1.0 / ng)
+    total = 0.0
+    for i in f:
+        m = i * i + f[:, None] ** 2 + f[None, :] ** 2
+        m = m[m > 0]
+        total += float(np.sum((kf * kf * m) ** (0.5 * slope)))
+    return variance * box_size ** 3 / total
+
+
+def linear_field(ng: int, box_size: float, slope: float, seed: int, amp=None, variance: float = 1.0):
+    """Gaussian field G with P(k) = A k^slope on the grid: G~ = FFT(W) sqrt(P ng^3 / L^3),
+    G = IFFT(G~) (numpy's normalized inverse).  Returns (G, G~, A)."""
+    if amp is None or amp <= 0:
+        amp = lognormal_amplitude(ng, box_size, slope, variance)
+    wk = np.fft.rfftn(white_noise(ng, seed))
+    kx, ky, kz = _k2_grid(ng, box_size)
+    k2 = kx * kx + ky * ky + kz * kz
+    k2[0, 0, 0] = 1.0
+    factor = np.sqrt(amp * k2 ** (0.5 * slope) * ng ** 3 / box_size ** 3)
+    factor[0, 0, 0] = 0.0
+    gk = wk * factor
+    return np.fft.irfftn(gk, s=(ng, ng, ng)), gk, amp
+
+
+def displacement_z(gk, box_size: float):
+    """psi_z = IFFT(i k_z / k^2 G~) (linear displacement, z component); the
+    z-Nyquist plane of psi~ is set to zero (its sign is ambiguous on the half grid)."""
+    ng = gk.shape[0]
+    kx, ky, kz = _k2_grid(ng, box_size)
+    k2 = kx * kx + ky * ky + kz * kz
+    k2[0, 0, 0] = 1.0
+    pk_ = gk * (1j * kz / k2)
+    pk_[0, 0, 0] = 0.0
+    pk_[:, :, ng // 2] = 0.0
+    return np.fft.irfftn(pk_, s=(ng, ng, ng))
+
+
+def lognormal_weights(G):
+    """Integer cell weights round(2^30 exp(G - sigma^2 / 2)), sigma^2 the grid variance of G."""
+    sig2 = float(np.mean(G * G) - np.mean(G) ** 2)
+    return np.rint(np.exp(G - 0.5 * sig2) * 2.0 ** 30).astype(np.int64)
+
+
+def place(q, box_size: float, psi_z, f_rsd: float, seed: int, n: int):
+    """Exactly n objects from integer cell weights q (ng^3): cell by inverse
+    CDF, uniform in the cell, z + f psi_z(cell), wrapped into [0, L)."""
+    ng = q.shape[0]
+    excl = np.zeros(q.size + 1, np.int64)
+    np.cumsum(q.reshape(-1), out=excl[1:])
+    pz = None if psi_z is None else np.ascontiguousarray(psi_z, dtype=np.float64)
+    pos = np.zeros((int(n), 3), np.float64)
+    rc = _load().oracle_place(_ptr(excl), int(ng), float(box_size), _ptr(pz), float(f_rsd), int(seed),
+                              int(n), _ptr(pos))
+    if rc != 0:
+        raise ValueError("oracle_place: bad arguments (%d)" % rc)
+    return pos
+
+
+def lognormal_catalog(n: int, box_size: float, ng: int, seed: int, slope: float = -1.5, amp=None,
+                      variance: float = 1.0, f_rsd: float = 0.75):
+    """The whole generator in FP64: linear field, log-normal transform,
+    integer cell weights, n objects, linear redshift-space displacement."""
+    G, gk, _ = linear_field(ng, box_size, slope, seed, amp, variance)
+    psi = displacement_z(gk, box_size) if f_rsd else None
+    return place(lognormal_weights(G), box_size, psi, f_rsd, seed, n)
