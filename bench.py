@@ -330,6 +330,49 @@ def plain_pass(pk, torch, cats, plans, stream):
     return out
 
 
+def generated_set(pk, torch, bp, specs, stream, runs):
+    """Mock -> P(k) wholly on the device: every mock of the set is drawn by the
+    library's log-normal generator (field grid = the mock's Nmesh) straight
+    into the batch buffers, then the captured graph is replayed."""
+    gens = {}
+    try:
+        for s in specs:
+            if s["nmesh"] not in gens:
+                gens[s["nmesh"]] = pk.LogNormalCatalog(MOCK_L, s["nmesh"], stream=stream)
+
+        def draw_all(round_):
+            for c in bp.classes:
+                for j, i in enumerate(c.index):
+                    a, b = int(c.offsets[j]), int(c.offsets[j + 1])
+                    gens[specs[i]["nmesh"]].draw(specs[i]["seed"] + 7919 * round_, b - a, out=c.pos[a:b])
+
+        draw_all(0)
+        bp.launch()
+        bp.results()
+        times, gen_dev = [], []
+        for r in range(runs):
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            draw_all(r + 1)
+            b.record(stream)
+            bp.launch()
+            bp.results()
+            times.append(time.perf_counter() - w0)
+            gen_dev.append(a.elapsed_time(b) / 1e3)
+        launches = sum(pk.load().pk_lognormal_launch_count(g.gen) for g in gens.values())
+    finally:
+        for g in gens.values():
+            g.close()
+    t = statistics.median(times)
+    return {"mock_to_pk_per_s": len(specs) / t, "ms_per_set": 1e3 * t,
+            "generate_device_ms_per_set": 1e3 * statistics.median(gen_dev),
+            "generator_launches_total": int(launches),
+            "note": "each mock drawn on the device (Philox field, log-normal weights, exact-integer "
+                    "inverse-CDF placement, RSD) into the batch buffers, then the graph replayed"}
+
+
 def measure_batched(pk, torch, world, rank, runs=5):
     """256 log-normal mocks (object counts log-uniform in [2e5, 4e6], Nmesh in
     {128, 192, 256}, CIC / TSC), L = 1000, dk = 0.01 to k_N, l = 0, 2, 4:
@@ -365,6 +408,7 @@ def measure_batched(pk, torch, world, rank, runs=5):
         launches = bp.launches_per_run
         classes = [{"nmesh": c.key[0], "window": c.key[1], "mocks": len(c.index),
                     "objects": int(c.offsets[-1]), "paint": "%s/%d" % c.choice} for c in bp.classes]
+        gen = generated_set(pk, torch, bp, specs, stream, runs)
     finally:
         bp.close()
     plans = {}
@@ -394,6 +438,7 @@ def measure_batched(pk, torch, world, rank, runs=5):
             "particles_painted_per_s_batched": world * nobj / tb,
             "max_rel_diff_batched_vs_plain": diff,
             "graph_launches_per_set": int(launches), "classes": classes,
+            "generated_on_device": gen,
             "autotune": {k: {c: round(t, 4) for c, t in v.items()} for k, v in tuner.timings.items()},
             "setup_s": setup_s}
 

@@ -255,6 +255,67 @@ long long pk_launch_count(pk_plan_t plan);
 pk_status pk_bin_static(const pk_config *cfg, const void *mesh, const void *mesh2, double *sums,
                         void *cuda_stream, char *err, size_t errlen);
 
+/* ---- Log-normal mock catalogs on the device ----
+ * The LogNormalCatalog source that the paper's tests and benchmarks paint
+ * (Sec. 3.2), over its Gaussian linear field, so that mock -> P(k) runs
+ * wholly on the GPU.  One draw with seed s:
+ *   1. white noise W on the ngrid^3 grid: Philox4x64-10 (Salmon et al.,
+ *      SC'11) with key (s, 0); cells 4b .. 4b+3 (flat index, z fastest) use the
+ *      four words of counter (b, 0, 0, 0) as two Box-Muller pairs, each word
+ *      mapped to the uniform ((w >> 40) + 1/2) 2^-24;
+ *   2. G~ = FFT(W) sqrt(A k^slope ngrid^3 / L^3) (DC removed), G = IFFT(G~)
+ *      normalized by 1 / ngrid^3: a Gaussian field of power A k^slope;
+ *   3. 1 + delta = exp(G - sigma^2 / 2), sigma^2 the grid variance of G,
+ *      held as integer cell weights round(2^30 (1 + delta));
+ *   4. exactly n objects (key (s, 1), counter (i, 0, 0, 0) for object i): the
+ *      cell by inverse CDF of t = floor(w0 total / 2^64) over the exact
+ *      integer prefix sums, a uniform offset inside the cell from w1..w3;
+ *   5. z += f_rsd psi_z(cell) with psi~_z = i k_z / k^2 G~ (the linear
+ *      displacement; its DC and z-Nyquist plane set to zero), wrapped into
+ *      [0, L).
+ * A draw depends only on (cfg, seed, n), not on the launch configuration. */
+typedef struct pk_lognormal_s *pk_lognormal_t;
+
+typedef struct {
+    double box_size;        /* L > 0                                              */
+    int ngrid;              /* field grid: even, 4 <= ngrid <= 2048               */
+    double slope;           /* P(k) = amp k^slope                                 */
+    double amp;             /* > 0: the amplitude; <= 0: chosen so that the grid
+                               variance (1 / L^3) sum_{k != 0} P(k) = variance   */
+    double variance;        /* used when amp <= 0; > 0                            */
+    double f_rsd;           /* z displacement factor (linear RSD); 0: none        */
+} pk_lognormal_config;
+
+/* Create a generator: validates cfg, allocates the grid buffers (about 16 +
+ * 8 (f_rsd != 0) bytes per cell, 16 bytes per cell for the weights and their
+ * prefix sums) and the cuFFT plans; all its work runs on `cuda_stream`.
+ * Errors: PK_EINVAL (bad cfg; message through pk_plan_error), PK_ENOMEM,
+ * PK_ECUDA, PK_ECUFFT.  On error *out is NULL. */
+pk_status pk_lognormal_plan(const pk_lognormal_config *cfg, void *cuda_stream, pk_lognormal_t *out);
+
+/* The Gaussian linear field G of seed `seed` (steps 1-2) into `field`: a dense
+ * ngrid^3 float array (z fastest), device or host memory.  Asynchronous on the
+ * generator's stream for device memory.  Errors: PK_EINVAL, PK_ECUDA, PK_ECUFFT. */
+pk_status pk_lognormal_field(pk_lognormal_t gen, uint64_t seed, float *field);
+
+/* Draw n objects of seed `seed` into `pos`: n x 3 float (x, y, z), device
+ * memory, in [0, L) (the layout PK_F32 of pk_paint).  Asynchronous on the
+ * generator's stream; `pos` is written when the stream passes the call.
+ * Errors: PK_EINVAL (n < 0, NULL pos), PK_ECUDA, PK_ECUFFT. */
+pk_status pk_lognormal_draw(pk_lognormal_t gen, uint64_t seed, int64_t n, float *pos);
+
+/* The amplitude A in use (the given one, or the one set from `variance`). */
+double pk_lognormal_amp(pk_lognormal_t gen);
+
+/* Number of the library's own kernels this generator has launched. */
+long long pk_lognormal_launch_count(pk_lognormal_t gen);
+
+/* Message of the last failed call on this generator ("" if none). */
+const char *pk_lognormal_error(pk_lognormal_t gen);
+
+/* Free the generator (waits for its stream).  NULL is a no-op. */
+pk_status pk_lognormal_destroy(pk_lognormal_t gen);
+
 /* Free everything the plan owns (waits for its stream).  NULL is a no-op. */
 pk_status pk_destroy(pk_plan_t plan);
 

@@ -278,7 +278,7 @@ def linear_field(ng: int, box_size: float, slope: float, seed: int, amp=None, va
     factor = np.sqrt(amp * k2 ** (0.5 * slope) * ng ** 3 / box_size ** 3)
     factor[0, 0, 0] = 0.0
     gk = wk * factor
-    return np.fft.irfftn(gk, s=(ng, ng, ng)), gk, amp
+    return np.fft.irfftn(gk, s=(ng, ng, ng), axes=(0, 1, 2)), gk, amp
 
 
 def displacement_z(gk, box_size: float):
@@ -291,7 +291,7 @@ def displacement_z(gk, box_size: float):
     pk_ = gk * (1j * kz / k2)
     pk_[0, 0, 0] = 0.0
     pk_[:, :, ng // 2] = 0.0
-    return np.fft.irfftn(pk_, s=(ng, ng, ng))
+    return np.fft.irfftn(pk_, s=(ng, ng, ng), axes=(0, 1, 2))
 
 
 def lognormal_weights(G):

@@ -42,7 +42,8 @@ WINDOWS = {"cic": PK_CIC, "tsc": PK_TSC, "pcs": PK_PCS}
 EXPORTED = ["pk_config_default", "pk_plan", "pk_paint", "pk_paint_many", "pk_compute",
             "pk_result", "pk_mesh", "pk_destroy", "pk_status_string", "pk_last_error",
             "pk_plan_error", "pk_enable_timing", "pk_stage_times", "pk_launch_count",
-            "pk_bin_static"]
+            "pk_bin_static", "pk_lognormal_plan", "pk_lognormal_field", "pk_lognormal_draw",
+            "pk_lognormal_amp", "pk_lognormal_launch_count", "pk_lognormal_error", "pk_lognormal_destroy"]
 STAGES = ["sort", "paint", "fft", "bin", "final"]
 
 
@@ -54,6 +55,13 @@ class pk_config(ctypes.Structure):
         ("poles_mask", ctypes.c_uint), ("los_axis", ctypes.c_int), ("precision", ctypes.c_int),
         ("subtract_shot", ctypes.c_int), ("fixed_scale_log2", ctypes.c_int), ("batch", ctypes.c_int),
         ("tile", ctypes.c_int), ("paint_variant", ctypes.c_int), ("capacity", ctypes.c_int64),
+    ]
+
+
+class pk_lognormal_config(ctypes.Structure):
+    _fields_ = [
+        ("box_size", ctypes.c_double), ("ngrid", ctypes.c_int), ("slope", ctypes.c_double),
+        ("amp", ctypes.c_double), ("variance", ctypes.c_double), ("f_rsd", ctypes.c_double),
     ]
 
 
@@ -117,6 +125,20 @@ def load():
         lib.pk_launch_count.restype = ctypes.c_longlong
         lib.pk_bin_static.argtypes = [ctypes.POINTER(pk_config), vp, vp, vp, vp, ctypes.c_char_p, ctypes.c_size_t]
         lib.pk_bin_static.restype = i
+        lib.pk_lognormal_plan.argtypes = [ctypes.POINTER(pk_lognormal_config), vp, ctypes.POINTER(vp)]
+        lib.pk_lognormal_plan.restype = i
+        lib.pk_lognormal_field.argtypes = [vp, ctypes.c_uint64, vp]
+        lib.pk_lognormal_field.restype = i
+        lib.pk_lognormal_draw.argtypes = [vp, ctypes.c_uint64, i64, vp]
+        lib.pk_lognormal_draw.restype = i
+        lib.pk_lognormal_amp.argtypes = [vp]
+        lib.pk_lognormal_amp.restype = ctypes.c_double
+        lib.pk_lognormal_launch_count.argtypes = [vp]
+        lib.pk_lognormal_launch_count.restype = ctypes.c_longlong
+        lib.pk_lognormal_error.argtypes = [vp]
+        lib.pk_lognormal_error.restype = ctypes.c_char_p
+        lib.pk_lognormal_destroy.argtypes = [vp]
+        lib.pk_lognormal_destroy.restype = i
         _lib = lib
     return _lib
 
@@ -319,6 +341,93 @@ class FFTPower:
         if self.plan:
             pk_destroy(self.plan)
             self.plan = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- log-normal mock catalogs on the device (pk_lognormal_*) ----
+
+def _check_ln(status, gen):
+    if status != PK_OK:
+        raise PkError(status, load().pk_lognormal_error(gen).decode())
+
+
+def pk_lognormal_plan(box_size, ngrid, slope=-1.5, amp=0.0, variance=1.0, f_rsd=0.75, stream=None):
+    """Generator of log-normal catalogs on an ngrid^3 field (see include/pk.h)."""
+    c = pk_lognormal_config(float(box_size), int(ngrid), float(slope), float(amp or 0.0), float(variance),
+                            float(f_rsd))
+    h = ctypes.c_void_p()
+    _check(load().pk_lognormal_plan(ctypes.byref(c), _stream_ptr(stream), ctypes.byref(h)))
+    return h
+
+
+def pk_lognormal_field(gen, seed, out):
+    """The Gaussian linear field of `seed` into `out` (torch tensor or numpy
+    array of ngrid^3 float32, device or host)."""
+    ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+    _check_ln(load().pk_lognormal_field(gen, int(seed), ptr), gen)
+
+
+def pk_lognormal_draw(gen, seed, n, out):
+    """Draw n objects of `seed` into `out`, a contiguous (>= n, 3) float32 device tensor."""
+    if tuple(out.shape[1:]) != (3,) or out.shape[0] < n or str(out.dtype) != "torch.float32" \
+            or not out.is_contiguous() or not out.is_cuda:
+        raise ValueError("out must be a contiguous (>= n, 3) float32 CUDA tensor")
+    _check_ln(load().pk_lognormal_draw(gen, int(seed), int(n), out.data_ptr()), gen)
+
+
+def pk_lognormal_amp(gen) -> float:
+    return float(load().pk_lognormal_amp(gen))
+
+
+def pk_lognormal_destroy(gen):
+    if gen:
+        _check(load().pk_lognormal_destroy(gen))
+
+
+class LogNormalCatalog:
+    """Device-resident log-normal mocks (the paper's LogNormalCatalog source):
+    ``LogNormalCatalog(L, ngrid).draw(seed, n)`` returns an (n, 3) float32 CUDA
+    tensor of positions in [0, L), generated wholly by the library's kernels."""
+
+    def __init__(self, box_size, ngrid, slope=-1.5, amp=0.0, variance=1.0, f_rsd=0.75, stream=None):
+        import torch
+        self.torch = torch
+        self.box_size, self.ngrid = float(box_size), int(ngrid)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.gen = pk_lognormal_plan(box_size, ngrid, slope, amp, variance, f_rsd, self.stream)
+
+    @property
+    def amp(self) -> float:
+        return pk_lognormal_amp(self.gen)
+
+    def draw(self, seed, n, out=None):
+        torch = self.torch
+        if out is None:
+            out = torch.empty((int(n), 3), dtype=torch.float32, device="cuda")
+        pk_lognormal_draw(self.gen, seed, n, out)
+        return out[: int(n)]
+
+    def field(self, seed):
+        torch = self.torch
+        out = torch.empty((self.ngrid,) * 3, dtype=torch.float32, device="cuda")
+        pk_lognormal_field(self.gen, seed, out)
+        return out
+
+    def close(self):
+        if self.gen:
+            pk_lognormal_destroy(self.gen)
+            self.gen = None
 
     def __enter__(self):
         return self

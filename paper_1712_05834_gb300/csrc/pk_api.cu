@@ -200,6 +200,8 @@ double sinc(double x) { return x == 0.0 ? 1.0 : sin(x) / x; }
 
 }  // namespace
 
+void pk::set_plan_error(const char *msg) { g_plan_error = msg ? msg : ""; }
+
 extern "C" {
 
 void pk_config_default(pk_config *c) {

@@ -9,6 +9,9 @@
 
 namespace pk {
 
+// Message of the last failed plan creation on this thread (pk_plan_error).
+void set_plan_error(const char *msg);
+
 // Geometry of the tile-sorted paint (Sec. 3.3.1 painting, Sec. 3.3.2 windows).
 // The mesh is cut into cubic tiles of T^3 cells.  Each object is sorted by
 // (home tile, boundary class); the paint CTA of a tile gathers its own objects
@@ -66,6 +69,8 @@ cudaError_t launch_sort_count(const void *pos, int dtype, const float *w, const 
                               uint32_t *rank, double *wsums, unsigned *wmax, cudaStream_t st);
 cudaError_t launch_scan(const uint32_t *in, int64_t n, uint32_t *out, uint32_t *tmp, int *launches,
                         cudaStream_t st);
+cudaError_t launch_scan64(const unsigned long long *in, int64_t n, unsigned long long *out,
+                          unsigned long long *tmp, int *launches, cudaStream_t st);
 cudaError_t launch_sort_scatter(const void *pos, int dtype, const float *w, const int64_t *item_off,
                                 int nitems, int64_t max_n, const PaintGeom &g, const uint32_t *off,
                                 const uint32_t *rank, float4 *sorted, int *err, cudaStream_t st);

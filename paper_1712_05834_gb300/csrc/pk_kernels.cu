@@ -262,47 +262,49 @@ k_sort_scatter(const void *__restrict__ pos, const float *__restrict__ w,
     }
 }
 
-// ---- exclusive scan of uint32 counts (totals < 2^32) ----
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total) {
-    __shared__ uint32_t wsum[kScanThreads / 32];
+// ---- exclusive scan of uint32 counts (totals < 2^32) or uint64 weights ----
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T *total) {
+    __shared__ T wsum[kScanThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t x = v;
+    T x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        const T y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
     if (lane == 31) wsum[wid] = x;
     __syncthreads();
     if (wid == 0) {
-        uint32_t s = lane < kScanThreads / 32 ? wsum[lane] : 0u;
+        T s = lane < kScanThreads / 32 ? wsum[lane] : (T)0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            const T y = __shfl_up_sync(0xffffffffu, s, o);
             if (lane >= o) s += y;
         }
         if (lane < kScanThreads / 32) wsum[lane] = s;
     }
     __syncthreads();
-    const uint32_t before = (wid > 0 ? wsum[wid - 1] : 0u) + x - v;
+    const T before = (wid > 0 ? wsum[wid - 1] : (T)0) + x - v;
     *total = wsum[kScanThreads / 32 - 1];
     __syncthreads();
     return before;
 }
 
 // out may alias in: every thread reads its own elements before writing them.
+template <typename T>
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_blocks(const uint32_t *in, int64_t n, uint32_t *out, uint32_t *bsum) {
+k_scan_blocks(const T *in, int64_t n, T *out, T *bsum) {
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
-    uint32_t v[kScanPer];
-    uint32_t s = 0;
+    T v[kScanPer];
+    T s = 0;
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) {
-        v[k] = base + k < n ? in[base + k] : 0u;
+        v[k] = base + k < n ? in[base + k] : (T)0;
         s += v[k];
     }
-    uint32_t total;
-    uint32_t run = block_exclusive_scan(s, &total);
+    T total;
+    T run = block_exclusive_scan<T>(s, &total);
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) {
         if (base + k < n) out[base + k] = run;
@@ -311,10 +313,11 @@ k_scan_blocks(const uint32_t *in, int64_t n, uint32_t *out, uint32_t *bsum) {
     if (threadIdx.x == 0) bsum[blockIdx.x] = total;
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_add(uint32_t *__restrict__ out, int64_t n, const uint32_t *__restrict__ bsum, int nb) {
+k_scan_add(T *__restrict__ out, int64_t n, const T *__restrict__ bsum, int nb) {
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
-    const uint32_t add = bsum[blockIdx.x];
+    const T add = bsum[blockIdx.x];
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k)
         if (base + k < n) out[base + k] += add;
@@ -1265,23 +1268,33 @@ size_t scan_tmp_elems(int64_t n) {
     return t + 2;
 }
 
-// out[0 .. n) = exclusive scan of in, out[n] = total.  tmp: scan_tmp_elems(n).
-cudaError_t launch_scan(const uint32_t *in, int64_t n, uint32_t *out, uint32_t *tmp, int *launches,
-                        cudaStream_t st) {
+template <typename T>
+static cudaError_t scan_impl(const T *in, int64_t n, T *out, T *tmp, int *launches, cudaStream_t st) {
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
     if (nb <= 1) {
-        k_scan_blocks<<<1, kScanThreads, 0, st>>>(in, n, out, out + n);
+        k_scan_blocks<T><<<1, kScanThreads, 0, st>>>(in, n, out, out + n);
         *launches += 1;
         return cudaGetLastError();
     }
     if (nb > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_scan_blocks<<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, out, tmp);
+    k_scan_blocks<T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, out, tmp);
     *launches += 1;
-    cudaError_t e = launch_scan(tmp, nb, tmp, tmp + nb + 1, launches, st);
+    cudaError_t e = scan_impl<T>(tmp, nb, tmp, tmp + nb + 1, launches, st);
     if (e != cudaSuccess) return e;
-    k_scan_add<<<(unsigned)nb, kScanThreads, 0, st>>>(out, n, tmp, (int)nb);
+    k_scan_add<T><<<(unsigned)nb, kScanThreads, 0, st>>>(out, n, tmp, (int)nb);
     *launches += 1;
     return cudaGetLastError();
+}
+
+// out[0 .. n) = exclusive scan of in, out[n] = total.  tmp: scan_tmp_elems(n).
+cudaError_t launch_scan(const uint32_t *in, int64_t n, uint32_t *out, uint32_t *tmp, int *launches,
+                        cudaStream_t st) {
+    return scan_impl<uint32_t>(in, n, out, tmp, launches, st);
+}
+
+cudaError_t launch_scan64(const unsigned long long *in, int64_t n, unsigned long long *out,
+                          unsigned long long *tmp, int *launches, cudaStream_t st) {
+    return scan_impl<unsigned long long>(in, n, out, tmp, launches, st);
 }
 
 size_t paint_smem_bytes(int T) {

@@ -97,7 +97,7 @@ def _c_layout(tmp_path, struct, fields):
     return int(out[0]), [int(v) for v in out[1:]]
 
 
-@pytest.mark.parametrize("name", ["pk_config", "pk_result_view"])
+@pytest.mark.parametrize("name", ["pk_config", "pk_result_view", "pk_lognormal_config"])
 def test_ctypes_structs_match_the_header(pk, tmp_path, name):
     cls = getattr(pk, name)
     fields = [f for f, _ in cls._fields_]
@@ -109,3 +109,24 @@ def test_ctypes_structs_match_the_header(pk, tmp_path, name):
 def test_config_default_new_fields(pk):
     c = pk.pk_config_default()
     assert c.paint_variant == pk.PK_PAINT_SORT and c.capacity == 0 and c.tile == 0
+
+
+@pytest.mark.parametrize("field,value,word", [
+    ("box_size", 0.0, "box_size"), ("ngrid", 7, "ngrid"), ("ngrid", 2, "ngrid"), ("ngrid", 4096, "ngrid"),
+    ("variance", 0.0, "variance"), ("slope", float("nan"), "slope"), ("f_rsd", float("inf"), "f_rsd"),
+])
+def test_lognormal_plan_rejects_bad_config(pk, field, value, word):
+    c = pk.pk_lognormal_config(1000.0, 32, -1.5, 0.0, 1.0, 0.75)
+    setattr(c, field, value)
+    h = ctypes.c_void_p()
+    assert pk.load().pk_lognormal_plan(ctypes.byref(c), None, ctypes.byref(h)) == pk.PK_EINVAL
+    assert not h.value
+    assert word in pk.load().pk_plan_error().decode()
+
+
+def test_lognormal_null_arguments(pk):
+    lib = pk.load()
+    assert lib.pk_lognormal_plan(None, None, None) == pk.PK_EINVAL
+    assert lib.pk_lognormal_draw(None, 1, 10, None) == pk.PK_EINVAL
+    assert lib.pk_lognormal_field(None, 1, None) == pk.PK_EINVAL
+    assert lib.pk_lognormal_destroy(None) == pk.PK_OK
