@@ -61,6 +61,8 @@ def _load():
         lib.oracle_mubin.restype = i64
         lib.oracle_bin.argtypes = [p, p, i, d, i, i, d, d, d, i, i] + [p] * 9
         lib.oracle_bin.restype = i
+        lib.oracle_bin_pair.argtypes = [p, p, p, p, i, d, i, i, d, d, d, d, i, i] + [p] * 9
+        lib.oracle_bin_pair.restype = i
         lib.oracle_paint_block.argtypes = [p, p, i64, d, i, i, d, p, i, p]
         lib.oracle_paint_block.restype = i
         lib.oracle_mode_counts.argtypes = [i, d, d, d, i, i, p, p]
@@ -173,6 +175,54 @@ def bin_modes(F1, F2, box_size, window, compensated, wsum, dk, kmin=0.0, kmax=No
         raise ValueError("oracle_bin: bad arguments")
     out["nk"], out["nmu"] = nk, nm
     return out
+
+
+def bin_cross(Fa1, Fa2, Fb1, Fb2, box_size, window, compensated, wsum_a, wsum_b, dk, kmin=0.0, kmax=None,
+              nmu=0):
+    """Raw bin sums of the cross power Re(delta_a conj(delta_b)) of two catalogs
+    painted on equal meshes (the auto-power loop with a second field)."""
+    Fa1 = np.ascontiguousarray(Fa1, dtype=np.complex128)
+    Fb1 = np.ascontiguousarray(Fb1, dtype=np.complex128)
+    N = Fa1.shape[0]
+    assert Fa1.shape == Fb1.shape == (N, N, N // 2 + 1)
+    Fa2 = None if Fa2 is None else np.ascontiguousarray(Fa2, dtype=np.complex128)
+    Fb2 = None if Fb2 is None else np.ascontiguousarray(Fb2, dtype=np.complex128)
+    nk = nbins(box_size, N, dk, kmin, kmax)
+    nm = max(int(nmu), 0)
+    out = {
+        "modes1d": np.zeros(nk, np.int64), "ksum1d": np.zeros(nk), "psum1d": np.zeros(nk),
+        "p2sum1d": np.zeros(nk), "p4sum1d": np.zeros(nk),
+        "modes2d": np.zeros(nk * max(nm, 1), np.int64), "ksum2d": np.zeros(nk * max(nm, 1)),
+        "musum2d": np.zeros(nk * max(nm, 1)), "psum2d": np.zeros(nk * max(nm, 1)),
+    }
+    rc = _load().oracle_bin_pair(
+        _ptr(Fa1), _ptr(Fa2), _ptr(Fb1), _ptr(Fb2), int(N), float(box_size), _order(window),
+        int(bool(compensated)), float(wsum_a), float(wsum_b), float(kmin), float(dk), int(nk), int(nm),
+        _ptr(out["modes1d"]), _ptr(out["ksum1d"]), _ptr(out["psum1d"]), _ptr(out["p2sum1d"]),
+        _ptr(out["p4sum1d"]), _ptr(out["modes2d"]), _ptr(out["ksum2d"]), _ptr(out["musum2d"]),
+        _ptr(out["psum2d"]))
+    if rc != 0:
+        raise ValueError("oracle_bin_pair: bad arguments")
+    out["nk"], out["nmu"] = nk, nm
+    return out
+
+
+def cross_power(pos_a, w_a, pos_b, w_b, box_size, nmesh, window="cic", interlaced=False, compensated=True,
+                dk=None, kmin=0.0, kmax=None, nmu=0):
+    """Cross power spectrum of two catalogs on the CPU in FP64 (no shot noise:
+    the catalogs are taken as independent samples)."""
+    sides = []
+    for pos, w in ((pos_a, w_a), (pos_b, w_b)):
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+        wsum = float(pos.shape[0]) if w is None else float(np.sum(np.asarray(w, dtype=np.float64)))
+        F1 = r2c(paint(pos, w, box_size, nmesh, window, 0.0))
+        F2 = r2c(paint(pos, w, box_size, nmesh, window, 0.5)) if interlaced else None
+        sides.append((F1, F2, wsum))
+    (Fa1, Fa2, wa), (Fb1, Fb2, wb) = sides
+    sums = bin_cross(Fa1, Fa2, Fb1, Fb2, box_size, window, compensated, wa, wb, dk, kmin, kmax, nmu)
+    res = finalize(sums, 0.0, False)
+    res["nk"], res["nmu"] = sums["nk"], sums["nmu"]
+    return res
 
 
 def finalize(sums, shot_noise: float, subtract_shot: bool = True):

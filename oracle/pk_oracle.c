@@ -28,6 +28,10 @@
  *                         (Eq. window-deconvolution), the interlacing combine,
  *                         |delta(k)|^2 averaged in k bins, (k, mu) bins and
  *                         Legendre multipoles l = 0, 2, 4.
+ *   oracle_bin_pair       the same loop for the cross power of two catalogs,
+ *                         P = L^3 Re(delta_a conj(delta_b)) (the cross-correlation
+ *                         of two painted fields, e.g. two tracers or a density
+ *                         and a momentum field, Sec. 3.3.1).
  *
  * The FFT between paint and bin is a library primitive (numpy's pocketfft),
  * called from the Python glue in oracle/__init__.py.
@@ -262,11 +266,38 @@ int64_t oracle_mubin(int64_t m, int64_t l, int64_t nmu)
  *   1D  (nk):      modes1d, ksum1d, psum1d, p2sum1d (P L2(mu)), p4sum1d (P L4(mu))
  *   2D  (nk*nmu):  modes2d, ksum2d, musum2d, psum2d   (only if nmu > 0)
  * Returns 0, or -1 on bad arguments. */
-int oracle_bin(const double *F1, const double *F2, int N, double L, int p,
-               int compensated, double wsum, double kmin, double dk, int nk,
-               int nmu, int64_t *modes1d, double *ksum1d, double *psum1d,
-               double *p2sum1d, double *p4sum1d, int64_t *modes2d,
-               double *ksum2d, double *musum2d, double *psum2d)
+/* delta(k) of one stored mode: the interlacing combine, the compensation and
+ * the division by the total weight, as listed above. */
+static void mode_delta(const double *F1, const double *F2, int64_t idx, int64_t ip, int64_t jp, int64_t l,
+                       int N, int p, int compensated, double wsum, double *re_out, double *im_out)
+{
+    double re = F1[2 * idx], im = F1[2 * idx + 1];
+    if (F2) {
+        double ph = M_PI * (double)(ip + jp + l) / (double)N;
+        double c = cos(ph), s = sin(ph);
+        double re2 = F2[2 * idx], im2 = F2[2 * idx + 1];
+        re = 0.5 * (re + (re2 * c - im2 * s));
+        im = 0.5 * (im + (re2 * s + im2 * c));
+    }
+    if (compensated) {
+        double W = pow(sinc(M_PI * (double)ip / N), p) *
+                   pow(sinc(M_PI * (double)jp / N), p) *
+                   pow(sinc(M_PI * (double)l / N), p);
+        re /= W;
+        im /= W;
+    }
+    *re_out = re / wsum;
+    *im_out = im / wsum;
+}
+
+/* The same loop for the cross power of two catalogs painted on equal meshes:
+ * P = L^3 Re(delta_a conj(delta_b)) with each delta formed as above from its
+ * own transforms (G1, G2) and total weight (wsum_b).  G1 = NULL gives the
+ * auto power of the first catalog. */
+int oracle_bin_pair(const double *F1, const double *F2, const double *G1, const double *G2, int N,
+                    double L, int p, int compensated, double wsum, double wsum_b, double kmin, double dk,
+                    int nk, int nmu, int64_t *modes1d, double *ksum1d, double *psum1d, double *p2sum1d,
+                    double *p4sum1d, int64_t *modes2d, double *ksum2d, double *musum2d, double *psum2d)
 {
     if (N < 2 || (N % 2) != 0 || L <= 0.0 || dk <= 0.0 || nk < 0 || nmu < 0)
         return -1;
@@ -284,24 +315,16 @@ int oracle_bin(const double *F1, const double *F2, int N, double L, int p,
                 if (b < 0 || b >= nk) continue;
                 double h = (l == 0 || l == NN / 2) ? 1.0 : 2.0;
                 int64_t idx = ((i * NN) + j) * Nh + l;
-                double re = F1[2 * idx], im = F1[2 * idx + 1];
-                if (F2) {
-                    double ph = M_PI * (double)(ip + jp + l) / (double)N;
-                    double c = cos(ph), s = sin(ph);
-                    double re2 = F2[2 * idx], im2 = F2[2 * idx + 1];
-                    re = 0.5 * (re + (re2 * c - im2 * s));
-                    im = 0.5 * (im + (re2 * s + im2 * c));
+                double re, im;
+                mode_delta(F1, F2, idx, ip, jp, l, N, p, compensated, wsum, &re, &im);
+                double P;
+                if (G1) {                            /* cross power with the second catalog */
+                    double reb, imb;
+                    mode_delta(G1, G2, idx, ip, jp, l, N, p, compensated, wsum_b, &reb, &imb);
+                    P = L3 * (re * reb + im * imb);
+                } else {
+                    P = L3 * (re * re + im * im);
                 }
-                if (compensated) {
-                    double W = pow(sinc(M_PI * (double)ip / N), p) *
-                               pow(sinc(M_PI * (double)jp / N), p) *
-                               pow(sinc(M_PI * (double)l / N), p);
-                    re /= W;
-                    im /= W;
-                }
-                re /= wsum;
-                im /= wsum;
-                double P = L3 * (re * re + im * im);
                 double k = kF * sqrt((double)m);
                 double mu = (double)l / sqrt((double)m);
                 double mu2 = mu * mu;
@@ -324,4 +347,14 @@ int oracle_bin(const double *F1, const double *F2, int N, double L, int p,
         }
     }
     return 0;
+}
+
+int oracle_bin(const double *F1, const double *F2, int N, double L, int p,
+               int compensated, double wsum, double kmin, double dk, int nk,
+               int nmu, int64_t *modes1d, double *ksum1d, double *psum1d,
+               double *p2sum1d, double *p4sum1d, int64_t *modes2d,
+               double *ksum2d, double *musum2d, double *psum2d)
+{
+    return oracle_bin_pair(F1, F2, NULL, NULL, N, L, p, compensated, wsum, 1.0, kmin, dk, nk, nmu,
+                           modes1d, ksum1d, psum1d, p2sum1d, p4sum1d, modes2d, ksum2d, musum2d, psum2d);
 }

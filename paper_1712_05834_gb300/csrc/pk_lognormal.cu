@@ -34,6 +34,7 @@ namespace pk {
 namespace {
 
 constexpr int kLnThreads = 256;
+constexpr int kCoarse = 1024;         // cells per block of the coarse CDF index
 
 struct Philox4x64 {
     unsigned long long w[4];
@@ -171,9 +172,21 @@ k_ln_weights(const float *__restrict__ g, int ng, long long pitch, const double 
     }
 }
 
+// coarse[k] = excl[min(k kCoarse, ncell)], k = 0 .. nblk: a small index that
+// stays in cache, so each object's search touches one 8 KB block of excl.
+__global__ void k_ln_coarse(const unsigned long long *__restrict__ excl, long long ncell, long long nblk,
+                            unsigned long long *__restrict__ coarse) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k <= nblk;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long c = k * kCoarse;
+        coarse[k] = excl[c < ncell ? c : ncell];
+    }
+}
+
 __global__ void __launch_bounds__(kLnThreads)
-k_ln_place(const unsigned long long *__restrict__ excl, int ng, double L, const float *__restrict__ psi,
-           long long pitch, float f_rsd, unsigned long long seed, long long n, float *__restrict__ pos) {
+k_ln_place(const unsigned long long *__restrict__ excl, const unsigned long long *__restrict__ coarse,
+           long long nblk, int ng, double L, const float *__restrict__ psi, long long pitch, float f_rsd,
+           unsigned long long seed, long long n, float *__restrict__ pos) {
     const long long ncell = (long long)ng * ng * ng;
     const unsigned long long total = excl[ncell];
     const double H = L / ng;
@@ -181,7 +194,13 @@ k_ln_place(const unsigned long long *__restrict__ excl, int ng, double L, const 
          i += (long long)gridDim.x * blockDim.x) {
         const Philox4x64 r = philox4x64((unsigned long long)i, seed, 1ull);
         const unsigned long long t = __umul64hi(r.w[0], total);
-        long long a = 0, b = ncell;                       // excl[a] <= t < excl[b]
+        long long ka = 0, kb = nblk;                      // coarse[ka] <= t < coarse[kb]
+        while (kb - ka > 1) {
+            const long long mid = ka + ((kb - ka) >> 1);
+            if (coarse[mid] <= t) ka = mid;
+            else kb = mid;
+        }
+        long long a = ka * kCoarse, b = kb * kCoarse < ncell ? kb * kCoarse : ncell;   // excl[a] <= t < excl[b]
         while (b - a > 1) {
             const long long mid = a + ((b - a) >> 1);
             if (excl[mid] <= t) a = mid;
@@ -226,6 +245,8 @@ struct pk_lognormal_s {
     float *psi = nullptr;            // psi_z (same layout), if f_rsd != 0
     unsigned long long *q = nullptr;     // cell weights
     unsigned long long *excl = nullptr;  // exclusive prefix sums, excl[ncell] = total
+    unsigned long long *coarse = nullptr;  // excl at every kCoarse-th cell (and at ncell)
+    long long nblk = 0;
     unsigned long long *scan_tmp = nullptr;
     double *stats = nullptr;
     cufftHandle fwd = 0, inv = 0;
@@ -263,7 +284,7 @@ void ln_free(pk_lognormal_s *G) {
     if (G->st || G->g) cudaStreamSynchronize(G->st);
     if (G->fwd_made) cufftDestroy(G->fwd);
     if (G->inv_made) cufftDestroy(G->inv);
-    void *dev[] = {G->g, G->psi, G->q, G->excl, G->scan_tmp, G->stats};
+    void *dev[] = {G->g, G->psi, G->q, G->excl, G->coarse, G->scan_tmp, G->stats};
     for (void *d : dev)
         if (d) cudaFree(d);
     delete G;
@@ -334,6 +355,9 @@ pk_status pk_lognormal_plan(const pk_lognormal_config *cfg, void *cuda_stream, p
     if (e == cudaSuccess)
         e = cudaMalloc(reinterpret_cast<void **>(&G->scan_tmp), sizeof(unsigned long long) * scan_tmp_elems(ncell));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&G->stats), 2 * sizeof(double));
+    G->nblk = (ncell + kCoarse - 1) / kCoarse;
+    if (e == cudaSuccess)
+        e = cudaMalloc(reinterpret_cast<void **>(&G->coarse), sizeof(unsigned long long) * (G->nblk + 1));
     if (e != cudaSuccess) {
         G->err = std::string("device allocation: ") + cudaGetErrorString(e);
         return bail(e == cudaErrorMemoryAllocation ? PK_ENOMEM : PK_ECUDA);
@@ -421,12 +445,15 @@ pk_status pk_lognormal_draw(pk_lognormal_t G, uint64_t seed, int64_t n, float *p
     LN_CUDA(G, cudaGetLastError());
     int launches = 0;
     LN_CUDA(G, launch_scan64(G->q, ncell, G->excl, G->scan_tmp, &launches, G->st));
+    k_ln_coarse<<<grid_of(G->nblk + 1, G->nsm), kLnThreads, 0, G->st>>>(G->excl, ncell, G->nblk, G->coarse);
+    LN_CUDA(G, cudaGetLastError());
     if (n > 0) {
-        k_ln_place<<<grid_of(n, G->nsm), kLnThreads, 0, G->st>>>(G->excl, ng, G->cfg.box_size, G->psi, G->pitch,
-                                                                  (float)G->cfg.f_rsd, seed, (long long)n, pos);
+        k_ln_place<<<grid_of(n, G->nsm), kLnThreads, 0, G->st>>>(G->excl, G->coarse, G->nblk, ng, G->cfg.box_size,
+                                                                  G->psi, G->pitch, (float)G->cfg.f_rsd, seed,
+                                                                  (long long)n, pos);
         LN_CUDA(G, cudaGetLastError());
     }
-    G->launches += 3 + launches + (n > 0);
+    G->launches += 4 + launches + (n > 0);
     return PK_OK;
 }
 
