@@ -253,19 +253,19 @@ def finalize(sums, shot_noise: float, subtract_shot: bool = True):
 
 def fft_power(pos, weights, box_size, nmesh, window="cic", interlaced=False,
               compensated=True, dk=None, kmin=0.0, kmax=None, nmu=0,
-              subtract_shot=True):
+              subtract_shot=True, values=None):
     """The whole path on the CPU in FP64: paint (one or two meshes), r2c FFT,
-    compensate + interlace, bin, multipoles, shot noise."""
+    compensate + interlace, bin, multipoles, shot noise.  ``values`` (V per
+    object, Sec. 3.3.1: F = [1 + delta'] V) paints W V but keeps the
+    normalization by sum W; the shot noise is L^3 sum (W V)^2 / (sum W)^2."""
     pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
-    if weights is None:
-        wsum = float(pos.shape[0])
-        w2sum = wsum
-    else:
-        w = np.asarray(weights, dtype=np.float64)
-        wsum = float(np.sum(w))
-        w2sum = float(np.sum(w * w))
-    F1 = r2c(paint(pos, weights, box_size, nmesh, window, 0.0))
-    F2 = r2c(paint(pos, weights, box_size, nmesh, window, 0.5)) if interlaced else None
+    w = np.ones(pos.shape[0]) if weights is None else np.asarray(weights, dtype=np.float64)
+    a = w if values is None else w * np.asarray(values, dtype=np.float64)
+    wsum = float(np.sum(w))
+    w2sum = float(np.sum(a * a))
+    amp = None if (weights is None and values is None) else a
+    F1 = r2c(paint(pos, amp, box_size, nmesh, window, 0.0))
+    F2 = r2c(paint(pos, amp, box_size, nmesh, window, 0.5)) if interlaced else None
     sums = bin_modes(F1, F2, box_size, window, compensated, wsum, dk, kmin, kmax, nmu)
     shot = box_size ** 3 * w2sum / wsum ** 2
     res = finalize(sums, shot, subtract_shot)
