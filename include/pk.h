@@ -176,6 +176,16 @@ pk_status pk_paint(pk_plan_t plan, const void *pos, int dtype,
 pk_status pk_paint_many(pk_plan_t plan, const void *pos, int dtype,
                         const float *weights, const int64_t *offsets, int nitems);
 
+/* Batched paint of a field value carried by the objects: the painted field is
+ * F = [1 + delta'] V (Sec. 3.3.1) with V a per-object value, e.g. a velocity
+ * component for the momentum field.  Each object deposits W V (W its weight,
+ * 1 if weights is NULL); the normalization keeps sum W, so P = L^3 |F~|^2 /
+ * (sum W)^2, and the shot noise is L^3 sum (W V)^2 / (sum W)^2.  values: n
+ * floats, device or host, in the order of pos.  Otherwise as pk_paint_many.
+ * Errors: as pk_paint_many, and PK_EINVAL for NULL values with objects. */
+pk_status pk_paint_values(pk_plan_t plan, const void *pos, int dtype, const float *weights,
+                          const float *values, const int64_t *offsets, int nitems);
+
 /* Transform, compensate, interlace and bin every painted catalog of the plan
  * (Sec. 3.4.1 with Eq. window-deconvolution).  Asynchronous on the plan's
  * stream; the results are copied to plan-owned host memory and become
@@ -187,6 +197,26 @@ pk_status pk_compute(pk_plan_t plan);
  * Errors: PK_ESTATE (no compute yet), PK_EINVAL (item out of range),
  * PK_EOVERFLOW (fixed-point headroom exceeded while painting), PK_ECUDA. */
 pk_status pk_result(pk_plan_t plan, int item, pk_result_view *out);
+
+/* Cross power spectrum of catalogs item_a and item_b of the last pk_compute
+ * (their transforms are still held by the plan): each stored mode contributes
+ * P = L^3 Re(delta_a conj(delta_b)), delta formed for each catalog as in
+ * pk_compute (interlacing combine, compensation, division by its own sum of
+ * weights), binned in the same k, (k, mu) bins and multipoles.  Cross powers of
+ * two fields painted from the same volume -- two tracers, or a density and a
+ * momentum field (Sec. 3.3.1, V(x) a velocity component) -- carry no shot
+ * noise term; none is subtracted.  item_a == item_b gives the auto power
+ * without shot-noise subtraction.  Asynchronous on the plan's stream; read the
+ * result with pk_cross_result.  Valid until the next pk_paint.
+ * Errors: PK_ESTATE (no pk_compute since the last paint), PK_EINVAL (item out
+ * of range), PK_ECUDA. */
+pk_status pk_cross(pk_plan_t plan, int item_a, int item_b);
+
+/* Wait for the last pk_cross and describe its result (same layout as
+ * pk_result; shot_noise = 0, wsum = sum of catalog a's weights, w2sum = sum of
+ * catalog b's weights).  The pointers stay valid until the next pk_cross or
+ * pk_destroy.  Errors: PK_ESTATE (no pk_cross yet), PK_EOVERFLOW, PK_ECUDA. */
+pk_status pk_cross_result(pk_plan_t plan, pk_result_view *out);
 
 /* Copy painted mesh `mesh` (0, or 1 = the interlaced mesh) of catalog `item`
  * into dst as a dense N x N x N array (z fastest) of the plan's precision

@@ -208,15 +208,18 @@ def bin_cross(Fa1, Fa2, Fb1, Fb2, box_size, window, compensated, wsum_a, wsum_b,
 
 
 def cross_power(pos_a, w_a, pos_b, w_b, box_size, nmesh, window="cic", interlaced=False, compensated=True,
-                dk=None, kmin=0.0, kmax=None, nmu=0):
+                dk=None, kmin=0.0, kmax=None, nmu=0, values_a=None, values_b=None):
     """Cross power spectrum of two catalogs on the CPU in FP64 (no shot noise:
-    the catalogs are taken as independent samples)."""
+    the catalogs are taken as independent samples).  values_a / values_b
+    paint W V with normalization by sum W, as in fft_power."""
     sides = []
-    for pos, w in ((pos_a, w_a), (pos_b, w_b)):
+    for pos, w, v in ((pos_a, w_a, values_a), (pos_b, w_b, values_b)):
         pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
-        wsum = float(pos.shape[0]) if w is None else float(np.sum(np.asarray(w, dtype=np.float64)))
-        F1 = r2c(paint(pos, w, box_size, nmesh, window, 0.0))
-        F2 = r2c(paint(pos, w, box_size, nmesh, window, 0.5)) if interlaced else None
+        wv = np.ones(pos.shape[0]) if w is None else np.asarray(w, dtype=np.float64)
+        wsum = float(np.sum(wv))
+        amp = w if v is None else wv * np.asarray(v, dtype=np.float64)
+        F1 = r2c(paint(pos, amp, box_size, nmesh, window, 0.0))
+        F2 = r2c(paint(pos, amp, box_size, nmesh, window, 0.5)) if interlaced else None
         sides.append((F1, F2, wsum))
     (Fa1, Fa2, wa), (Fb1, Fb2, wb) = sides
     sums = bin_cross(Fa1, Fa2, Fb1, Fb2, box_size, window, compensated, wa, wb, dk, kmin, kmax, nmu)

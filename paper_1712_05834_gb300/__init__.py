@@ -42,7 +42,7 @@ WINDOWS = {"cic": PK_CIC, "tsc": PK_TSC, "pcs": PK_PCS}
 EXPORTED = ["pk_config_default", "pk_plan", "pk_paint", "pk_paint_many", "pk_compute",
             "pk_result", "pk_mesh", "pk_destroy", "pk_status_string", "pk_last_error",
             "pk_plan_error", "pk_enable_timing", "pk_stage_times", "pk_launch_count",
-            "pk_bin_static", "pk_lognormal_plan", "pk_lognormal_field", "pk_lognormal_draw",
+            "pk_bin_static", "pk_cross", "pk_cross_result", "pk_paint_values", "pk_lognormal_plan", "pk_lognormal_field", "pk_lognormal_draw",
             "pk_lognormal_amp", "pk_lognormal_launch_count", "pk_lognormal_error", "pk_lognormal_destroy"]
 STAGES = ["sort", "paint", "fft", "bin", "final"]
 
@@ -103,10 +103,16 @@ def load():
         lib.pk_paint.restype = i
         lib.pk_paint_many.argtypes = [vp, vp, i, vp, ctypes.POINTER(ctypes.c_int64), i]
         lib.pk_paint_many.restype = i
+        lib.pk_paint_values.argtypes = [vp, vp, i, vp, vp, ctypes.POINTER(ctypes.c_int64), i]
+        lib.pk_paint_values.restype = i
         lib.pk_compute.argtypes = [vp]
         lib.pk_compute.restype = i
         lib.pk_result.argtypes = [vp, i, ctypes.POINTER(pk_result_view)]
         lib.pk_result.restype = i
+        lib.pk_cross.argtypes = [vp, i, i]
+        lib.pk_cross.restype = i
+        lib.pk_cross_result.argtypes = [vp, ctypes.POINTER(pk_result_view)]
+        lib.pk_cross_result.restype = i
         lib.pk_mesh.argtypes = [vp, i, i, vp]
         lib.pk_mesh.restype = i
         lib.pk_destroy.argtypes = [vp]
@@ -265,6 +271,17 @@ def pk_paint_many(plan, pos, offsets, weights=None):
                                 off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(off) - 1), plan)
 
 
+def pk_paint_values(plan, pos, values, offsets=None, weights=None):
+    """Paint the field value V of every object (e.g. a velocity component:
+    the momentum field); normalization by sum W, deposits W V."""
+    ptr, code, n = _array_info(pos)
+    off = np.ascontiguousarray(np.asarray([0, n] if offsets is None else offsets, dtype=np.int64))
+    if off[-1] != n:
+        raise ValueError("offsets[-1] must equal the number of objects")
+    _check(load().pk_paint_values(plan, ptr, code, _weights_ptr(weights, n), _weights_ptr(values, n),
+                                  off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(off) - 1), plan)
+
+
 def pk_compute(plan):
     _check(load().pk_compute(plan), plan)
 
@@ -275,10 +292,7 @@ def _arr(ptr, n, dtype=np.float64):
     return np.ctypeslib.as_array(ptr, shape=(n,)).astype(dtype, copy=True)
 
 
-def pk_result(plan, item=0) -> dict:
-    """Result of catalog ``item`` of the last compute, copied into numpy arrays."""
-    v = pk_result_view()
-    _check(load().pk_result(plan, int(item), ctypes.byref(v)), plan)
+def _view_dict(v) -> dict:
     nk, nmu = v.nk, v.nmu
     out = {
         "nk": nk, "nmu": nmu,
@@ -296,6 +310,22 @@ def pk_result(plan, item=0) -> dict:
         out["power2d"] = _arr(v.pkmu, nk * nmu).reshape(nk, nmu)
         out["modes2d"] = _arr(v.modes2d, nk * nmu, np.int64).reshape(nk, nmu)
     return out
+
+
+def pk_result(plan, item=0) -> dict:
+    """Result of catalog ``item`` of the last compute, copied into numpy arrays."""
+    v = pk_result_view()
+    _check(load().pk_result(plan, int(item), ctypes.byref(v)), plan)
+    return _view_dict(v)
+
+
+def pk_cross(plan, item_a, item_b) -> dict:
+    """Cross power of two catalogs of the last compute (no shot noise), as a
+    dict like pk_result's (wsum: catalog a's sum of weights, w2sum: b's)."""
+    _check(load().pk_cross(plan, int(item_a), int(item_b)), plan)
+    v = pk_result_view()
+    _check(load().pk_cross_result(plan, ctypes.byref(v)), plan)
+    return _view_dict(v)
 
 
 def pk_mesh(plan, item, mesh, nmesh, f64=False):

@@ -69,6 +69,9 @@ struct pk_plan_s {
     int G_total = 0;
     void *d_partial = nullptr;
     double *d_sums2 = nullptr, *d_res = nullptr, *h_res = nullptr;
+    double *d_xres = nullptr, *h_xres = nullptr;   // cross-power result block
+    cudaEvent_t xdone = nullptr;
+    int xdone_valid = 0, xcomputed = 0;
     unsigned long long *d_modes1d = nullptr, *d_modes2d = nullptr;
 
     std::vector<int> kedge;
@@ -127,10 +130,12 @@ void free_plan(pk_plan_s *p) {
     void *dev[] = {p->mesh, p->d_count, p->d_off, p->d_scan_tmp, p->d_rank, p->d_sorted,
                    p->d_stage, p->d_item_off, p->d_wsums, p->d_wmax, p->d_cw, p->d_ph,
                    p->d_kedge, p->d_partial, p->d_sums2, p->d_res, p->d_modes1d, p->d_modes2d,
-                   p->d_err, p->d_acc, p->fft_work};
+                   p->d_err, p->d_acc, p->fft_work, p->d_xres};
     for (void *d : dev)
         if (d) cudaFree(d);
     if (p->h_res) cudaFreeHost(p->h_res);
+    if (p->h_xres) cudaFreeHost(p->h_xres);
+    if (p->xdone) cudaEventDestroy(p->xdone);
     if (p->done) cudaEventDestroy(p->done);
     for (cudaEvent_t e : p->tev)
         if (e) cudaEventDestroy(e);
@@ -379,6 +384,9 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
     PK_CUDA(P, dev_alloc(&P->d_sums2, sizeof(double) * (size_t)(reduce_chunks(P->G_total) + P->B) * bg.nh));
     PK_CUDA(P, dev_alloc(&P->d_res, sizeof(double) * (size_t)P->B * fg.RL));
     PK_CUDA(P, cudaMallocHost(reinterpret_cast<void **>(&P->h_res), sizeof(double) * (size_t)P->B * fg.RL));
+    PK_CUDA(P, dev_alloc(&P->d_xres, sizeof(double) * (size_t)fg.RL));
+    PK_CUDA(P, cudaMallocHost(reinterpret_cast<void **>(&P->h_xres), sizeof(double) * (size_t)fg.RL));
+    PK_CUDA(P, cudaEventCreateWithFlags(&P->xdone, cudaEventDisableTiming));
     const int nq = nmu > 0 ? nmu : 1;
     if (c.paint_variant == PK_PAINT_ATOMIC) {
         const size_t acc_bytes = sizeof(unsigned long long) * (size_t)P->B * P->nm * P->N * P->N * P->N;
@@ -521,7 +529,7 @@ pk_status pk_plan(const pk_config *cfg, void *cuda_stream, pk_plan_t *out) {
 }
 
 // The atomic variant: weight sums and deposits in one pass, then conversion.
-static pk_status paint_atomic(pk_plan_s *P, const void *dpos, int dtype, const float *dw,
+static pk_status paint_atomic(pk_plan_s *P, const void *dpos, int dtype, const float *dw, const float *dv,
                               const int64_t *offsets, int nitems, int64_t max_n, int accumulate) {
     const cudaStream_t st = P->st;
     const int tm = P->timing && !capturing(st);
@@ -533,7 +541,7 @@ static pk_status paint_atomic(pk_plan_s *P, const void *dpos, int dtype, const f
         PK_CUDA(P, cudaMemsetAsync(P->d_wmax, 0, sizeof(unsigned) * nitems, st));
     }
     if (tm) PK_CUDA(P, cudaEventRecord(P->tev[1], st));   // no sort stage
-    PK_CUDA(P, launch_paint_atomic(dpos, dtype, dw, P->d_item_off, nitems, max_n, P->pg, P->p, P->nm, P->S,
+    PK_CUDA(P, launch_paint_atomic(dpos, dtype, dw, dv, P->d_item_off, nitems, max_n, P->pg, P->p, P->nm, P->S,
                                    P->d_acc, P->d_wsums, P->d_wmax, st));
     PK_CUDA(P, launch_acc_to_mesh(P->d_acc, nitems, P->nm, P->N, P->S, P->f64, P->mesh,
                                   P->nm * P->mesh_reals, P->mesh_reals, accumulate, P->nsm, st));
@@ -546,7 +554,7 @@ static pk_status paint_atomic(pk_plan_s *P, const void *dpos, int dtype, const f
 }
 
 static pk_status paint_impl(pk_plan_s *P, const void *pos, int dtype, const float *weights,
-                            const int64_t *offsets, int nitems, int accumulate) {
+                            const float *values, const int64_t *offsets, int nitems, int accumulate) {
     if (dtype != PK_F32 && dtype != PK_F64 && dtype != PK_F32X4)
         return fail(P, PK_EINVAL, "dtype must be PK_F32, PK_F64 or PK_F32X4");
     if (dtype == PK_F32X4 && weights)
@@ -569,19 +577,23 @@ static pk_status paint_impl(pk_plan_s *P, const void *pos, int dtype, const floa
     // stage host inputs on the device
     const void *dpos = pos;
     const float *dw = weights;
+    const float *dv = values;
     const bool pos_dev = ntot == 0 || is_device_pointer(pos);
     const bool w_dev = !weights || ntot == 0 || is_device_pointer(weights);
+    const bool v_dev = !values || ntot == 0 || is_device_pointer(values);
     if (pos_dev && dtype == PK_F32X4 && (reinterpret_cast<uintptr_t>(pos) % 16) != 0)
         return fail(P, PK_EINVAL, "PK_F32X4 positions must be 16-byte aligned");
     if (pos_dev && dtype == PK_F64 && (reinterpret_cast<uintptr_t>(pos) % 8) != 0)
         return fail(P, PK_EINVAL, "PK_F64 positions must be 8-byte aligned");
-    if ((!pos_dev || !w_dev) && capturing(st))
-        return fail(P, PK_EINVAL, "host positions or weights cannot be painted under stream capture");
-    if (!pos_dev || !w_dev) {
+    if ((!pos_dev || !w_dev || !v_dev) && capturing(st))
+        return fail(P, PK_EINVAL, "host positions, weights or values cannot be painted under stream capture");
+    if (!pos_dev || !w_dev || !v_dev) {
         const size_t pbytes = pos_dev ? 0 : (size_t)ntot * rb;
         const size_t pad = (pbytes + 255) / 256 * 256;
         const size_t wbytes = w_dev ? 0 : (size_t)ntot * sizeof(float);
-        const size_t need = pad + wbytes;
+        const size_t wpad = (wbytes + 255) / 256 * 256;
+        const size_t vbytes = v_dev ? 0 : (size_t)ntot * sizeof(float);
+        const size_t need = pad + wpad + vbytes;
         if (need > P->stage_cap) {
             PK_CUDA(P, cudaStreamSynchronize(st));
             if (P->d_stage) cudaFree(P->d_stage);
@@ -599,12 +611,16 @@ static pk_status paint_impl(pk_plan_s *P, const void *pos, int dtype, const floa
             PK_CUDA(P, cudaMemcpyAsync(sb + pad, weights, wbytes, cudaMemcpyHostToDevice, st));
             dw = reinterpret_cast<const float *>(sb + pad);
         }
+        if (!v_dev) {
+            PK_CUDA(P, cudaMemcpyAsync(sb + pad + wpad, values, vbytes, cudaMemcpyHostToDevice, st));
+            dv = reinterpret_cast<const float *>(sb + pad + wpad);
+        }
     }
 
     if (ntot >= (int64_t)0xffffffffLL)
         return fail(P, PK_EINVAL, "at most 2^32 - 2 objects per paint call");
     if (P->cfg.paint_variant == PK_PAINT_ATOMIC)
-        return paint_atomic(P, dpos, dtype, dw, offsets, nitems, max_n, accumulate);
+        return paint_atomic(P, dpos, dtype, dw, dv, offsets, nitems, max_n, accumulate);
     if (ntot > P->sorted_cap && capturing(st))
         return fail(P, PK_EINVAL, "objects exceed the plan's capacity under stream capture");
     if (ntot > P->sorted_cap) {                 // grow the key-ordered copy (rare)
@@ -628,13 +644,13 @@ static pk_status paint_impl(pk_plan_s *P, const void *pos, int dtype, const floa
         PK_CUDA(P, cudaMemsetAsync(P->d_wsums, 0, sizeof(double) * 4 * nitems, st));
         PK_CUDA(P, cudaMemsetAsync(P->d_wmax, 0, sizeof(unsigned) * nitems, st));
     }
-    PK_CUDA(P, launch_sort_count(dpos, dtype, dw, P->d_item_off, nitems, max_n, P->pg, P->d_count,
+    PK_CUDA(P, launch_sort_count(dpos, dtype, dw, dv, P->d_item_off, nitems, max_n, P->pg, P->d_count,
                                  P->d_rank, P->d_wsums, P->d_wmax, st));
     PK_CUDA(P, launch_scan(P->d_count, nkeys, P->d_off, P->d_scan_tmp, &launches, st));
-    PK_CUDA(P, launch_sort_scatter(dpos, dtype, dw, P->d_item_off, nitems, max_n, P->pg, P->d_off,
+    PK_CUDA(P, launch_sort_scatter(dpos, dtype, dw, dv, P->d_item_off, nitems, max_n, P->pg, P->d_off,
                                    P->d_rank, P->d_sorted, P->d_err, st));
     if (tm) PK_CUDA(P, cudaEventRecord(P->tev[1], st));
-    const int unit_weights = dw == nullptr && dtype != PK_F32X4;
+    const int unit_weights = dw == nullptr && dv == nullptr && dtype != PK_F32X4;
     PK_CUDA(P, launch_paint_tiles(P->d_sorted, P->d_off, nitems, P->pg, P->p, P->nm, P->S, P->f64,
                                   P->d_wmax, unit_weights, P->mesh, P->nm * P->mesh_reals,
                                   P->mesh_reals, accumulate, st));
@@ -653,7 +669,7 @@ pk_status pk_paint(pk_plan_t P, const void *pos, int dtype, const float *weights
     P->err.clear();
     if (n < 0) return fail(P, PK_EINVAL, "n must be >= 0");
     const int64_t off[2] = {0, n};
-    return paint_impl(P, pos, dtype, weights, off, 1, accumulate ? 1 : 0);
+    return paint_impl(P, pos, dtype, weights, nullptr, off, 1, accumulate ? 1 : 0);
 }
 
 pk_status pk_paint_many(pk_plan_t P, const void *pos, int dtype, const float *weights,
@@ -661,7 +677,16 @@ pk_status pk_paint_many(pk_plan_t P, const void *pos, int dtype, const float *we
     if (!P) return PK_EINVAL;
     P->err.clear();
     if (!offsets) return fail(P, PK_EINVAL, "offsets is NULL");
-    return paint_impl(P, pos, dtype, weights, offsets, nitems, 0);
+    return paint_impl(P, pos, dtype, weights, nullptr, offsets, nitems, 0);
+}
+
+pk_status pk_paint_values(pk_plan_t P, const void *pos, int dtype, const float *weights, const float *values,
+                          const int64_t *offsets, int nitems) {
+    if (!P) return PK_EINVAL;
+    P->err.clear();
+    if (!offsets) return fail(P, PK_EINVAL, "offsets is NULL");
+    if (!values && offsets[nitems > 0 ? nitems : 0] > 0) return fail(P, PK_EINVAL, "values is NULL");
+    return paint_impl(P, pos, dtype, weights, values, offsets, nitems, 0);
 }
 
 pk_status pk_compute(pk_plan_t P) {
@@ -721,6 +746,8 @@ pk_status pk_compute(pk_plan_t P) {
     return PK_OK;
 }
 
+static pk_status fill_view(pk_plan_s *P, const double *r, pk_result_view *out);
+
 pk_status pk_result(pk_plan_t P, int item, pk_result_view *out) {
     if (!P) return PK_EINVAL;
     P->err.clear();
@@ -728,7 +755,46 @@ pk_status pk_result(pk_plan_t P, int item, pk_result_view *out) {
     if (P->computed < 1) return fail(P, PK_ESTATE, "no compute yet");
     if (item < 0 || item >= P->computed) return fail(P, PK_EINVAL, "item out of range");
     if (P->done_valid) PK_CUDA(P, cudaEventSynchronize(P->done));
-    const double *r = P->h_res + (size_t)item * P->fg.RL;
+    return fill_view(P, P->h_res + (size_t)item * P->fg.RL, out);
+}
+
+pk_status pk_cross(pk_plan_t P, int item_a, int item_b) {
+    if (!P) return PK_EINVAL;
+    P->err.clear();
+    if (!P->transformed || P->computed < 1) return fail(P, PK_ESTATE, "pk_cross needs a pk_compute first");
+    if (item_a < 0 || item_a >= P->computed || item_b < 0 || item_b >= P->computed)
+        return fail(P, PK_EINVAL, "item out of range");
+    const cudaStream_t st = P->st;
+    const long long item_c = (long long)P->nm * P->mesh_reals / 2;   // complex elements per catalog
+    const long long mesh_c = P->mesh_reals / 2;
+    const size_t csz = 2 * P->esz;
+    const char *base = reinterpret_cast<const char *>(P->mesh);
+    PK_CUDA(P, launch_bin_cross(base + (size_t)item_a * item_c * csz, base + (size_t)item_b * item_c * csz, P->f64,
+                                P->cfg.interlaced, mesh_c, P->G_total, P->bg, P->d_cw, P->d_ph, P->d_kedge,
+                                P->d_partial, st));
+    PK_CUDA(P, launch_bin_reduce(P->d_partial, P->f64, P->G_total, P->bg.nh, 1, P->d_sums2, st));
+    PK_CUDA(P, launch_finalize_cross(P->d_sums2, P->G_total, P->d_modes1d, P->d_modes2d, P->d_wsums, P->d_err,
+                                     P->fg, item_a, item_b, P->d_xres, st));
+    P->launches += 3;
+    PK_CUDA(P, cudaMemcpyAsync(P->h_xres, P->d_xres, sizeof(double) * (size_t)P->fg.RL, cudaMemcpyDeviceToHost,
+                               st));
+    const int cap = capturing(st);
+    if (!cap) PK_CUDA(P, cudaEventRecord(P->xdone, st));
+    P->xdone_valid = !cap;
+    P->xcomputed = 1;
+    return PK_OK;
+}
+
+pk_status pk_cross_result(pk_plan_t P, pk_result_view *out) {
+    if (!P) return PK_EINVAL;
+    P->err.clear();
+    if (!out) return fail(P, PK_EINVAL, "out is NULL");
+    if (!P->xcomputed) return fail(P, PK_ESTATE, "no pk_cross yet");
+    if (P->xdone_valid) PK_CUDA(P, cudaEventSynchronize(P->xdone));
+    return fill_view(P, P->h_xres, out);
+}
+
+static pk_status fill_view(pk_plan_s *P, const double *r, pk_result_view *out) {
     const ResultLayout &rl = P->rl;
     const int nk = P->bg.nk, nmu = P->bg.nmu;
     memset(out, 0, sizeof(*out));

@@ -64,16 +64,19 @@ size_t scan_tmp_elems(int64_t n);
 // dst[0 .. n) = src[0 .. n) for a host array src, through kernel parameters
 // (the host array may be reused as soon as the call returns).
 cudaError_t launch_upload_i64(int64_t *dst, const int64_t *src, int n, int *launches, cudaStream_t st);
-cudaError_t launch_sort_count(const void *pos, int dtype, const float *w, const int64_t *item_off,
-                              int nitems, int64_t max_n, const PaintGeom &g, uint32_t *count,
-                              uint32_t *rank, double *wsums, unsigned *wmax, cudaStream_t st);
+// w: weights (normalization; NULL = 1), vals: painted values V (NULL = 1);
+// each object deposits W V and the sums keep sum W, sum (W V)^2, sum |W V|.
+cudaError_t launch_sort_count(const void *pos, int dtype, const float *w, const float *vals,
+                              const int64_t *item_off, int nitems, int64_t max_n, const PaintGeom &g,
+                              uint32_t *count, uint32_t *rank, double *wsums, unsigned *wmax, cudaStream_t st);
 cudaError_t launch_scan(const uint32_t *in, int64_t n, uint32_t *out, uint32_t *tmp, int *launches,
                         cudaStream_t st);
 cudaError_t launch_scan64(const unsigned long long *in, int64_t n, unsigned long long *out,
                           unsigned long long *tmp, int *launches, cudaStream_t st);
-cudaError_t launch_sort_scatter(const void *pos, int dtype, const float *w, const int64_t *item_off,
-                                int nitems, int64_t max_n, const PaintGeom &g, const uint32_t *off,
-                                const uint32_t *rank, float4 *sorted, int *err, cudaStream_t st);
+cudaError_t launch_sort_scatter(const void *pos, int dtype, const float *w, const float *vals,
+                                const int64_t *item_off, int nitems, int64_t max_n, const PaintGeom &g,
+                                const uint32_t *off, const uint32_t *rank, float4 *sorted, int *err,
+                                cudaStream_t st);
 cudaError_t launch_paint_tiles(const float4 *sorted, const uint32_t *off, int nitems,
                                const PaintGeom &g, int window, int nmesh, int S, int f64,
                                const unsigned *wmax, int unit_weights, void *mesh,
@@ -82,10 +85,10 @@ cudaError_t launch_paint_tiles(const float4 *sorted, const uint32_t *off, int ni
 
 // Direct atomic paint into dense int64 accumulators (nitems x nmesh x N^3,
 // zero on entry), then conversion into the r2c mesh layout (clears them).
-cudaError_t launch_paint_atomic(const void *pos, int dtype, const float *w, const int64_t *item_off,
-                                int nitems, int64_t max_n, const PaintGeom &g, int window, int nmesh,
-                                int S, unsigned long long *acc, double *wsums, unsigned *wmax,
-                                cudaStream_t st);
+cudaError_t launch_paint_atomic(const void *pos, int dtype, const float *w, const float *vals,
+                                const int64_t *item_off, int nitems, int64_t max_n, const PaintGeom &g,
+                                int window, int nmesh, int S, unsigned long long *acc, double *wsums,
+                                unsigned *wmax, cudaStream_t st);
 cudaError_t launch_acc_to_mesh(unsigned long long *acc, int nitems, int nmesh, int N, int S, int f64,
                                void *mesh, long long item_stride, long long mesh_stride, int accumulate,
                                int nsm, cudaStream_t st);
@@ -94,6 +97,11 @@ cudaError_t launch_bin(const void *mesh, int f64, int interlaced, long long item
                        long long mesh_stride_c, int nitems, int ctas_per_item,
                        const BinGeom &g, const void *cw, const void *ph, const int *kedge,
                        void *partial, cudaStream_t st);
+// Cross power of two catalogs: mesh_a / mesh_b point at each catalog's first
+// mesh (the interlaced one follows at mesh_stride_c); one item, `ctas` CTAs.
+cudaError_t launch_bin_cross(const void *mesh_a, const void *mesh_b, int f64, int interlaced,
+                             long long mesh_stride_c, int ctas, const BinGeom &g, const void *cw,
+                             const void *ph, const int *kedge, void *partial, cudaStream_t st);
 size_t bin_smem_bytes(const BinGeom &g, int f64);
 int bin_ctas_per_sm(const BinGeom &g, int f64);
 int bin_threads();
@@ -103,6 +111,10 @@ cudaError_t launch_bin_reduce(const void *partial, int f64, int G, int nh, int n
 cudaError_t launch_finalize(const double *sums2, int G, const unsigned long long *modes1d,
                             const unsigned long long *modes2d, const double *wsums, const int *err,
                             const FinalGeom &f, int nitems, double *res, cudaStream_t st);
+
+cudaError_t launch_finalize_cross(const double *sums2, int G, const unsigned long long *modes1d,
+                                  const unsigned long long *modes2d, const double *wsums, const int *err,
+                                  const FinalGeom &f, int item_a, int item_b, double *res, cudaStream_t st);
 
 cudaError_t launch_geom_hist(const BinGeom &g, unsigned long long *H, unsigned long long *HL,
                              cudaStream_t st);

@@ -106,7 +106,8 @@ template <typename R>
 struct Obj {
     R s[3];
     float e[3];       // residual of s (FP32 positions), 0 for FP64 positions
-    float w;
+    float w;          // weight W (normalization: sum W)
+    float a;          // painted amplitude W V (V: the painted value, 1 by default)
 };
 
 template <int DT>
@@ -116,7 +117,8 @@ struct PosReal<PK_F64> { using type = double; };
 
 template <int DT>
 __device__ __forceinline__ Obj<typename PosReal<DT>::type> load_obj(const void *pos, const float *w,
-                                                                    int64_t i, const PaintGeom &g) {
+                                                                    const float *vals, int64_t i,
+                                                                    const PaintGeom &g) {
     using R = typename PosReal<DT>::type;
     Obj<R> o;
     if (DT == PK_F32X4) {
@@ -139,6 +141,7 @@ __device__ __forceinline__ Obj<typename PosReal<DT>::type> load_obj(const void *
         o.e[0] = o.e[1] = o.e[2] = 0.0f;
         o.w = w ? __ldg(w + i) : 1.0f;
     }
+    o.a = vals ? o.w * __ldg(vals + i) : o.w;
     return o;
 }
 
@@ -171,8 +174,9 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
-// Block reduction of the weight sums: wsums[4 * item + {0,1,2}] = sum w,
-// sum w^2, sum |w|; wmax[item] = max |w| (float bits).
+// Block reduction of the weight sums: wsums[4 * item + {0,1,2}] = sum W,
+// sum (W V)^2, sum |W V|; wmax[item] = max |W V| (float bits), with W the
+// weight and W V the painted amplitude.
 __device__ __forceinline__ void flush_wsums(double sw, double sw2, double swa, float mw, bool weighted,
                                             int item, int64_t n_item, double *__restrict__ wsums,
                                             unsigned *__restrict__ wmax) {
@@ -209,7 +213,7 @@ __device__ __forceinline__ void flush_wsums(double sw, double sw2, double swa, f
 // Tile sort, pass 1: key counts and ranks, plus the weight sums.
 template <int DT, bool WEIGHTED>
 __global__ void __launch_bounds__(kCountThreads)
-k_sort_count(const void *__restrict__ pos, const float *__restrict__ w,
+k_sort_count(const void *__restrict__ pos, const float *__restrict__ w, const float *__restrict__ vals,
              const int64_t *__restrict__ item_off, PaintGeom g, uint32_t *__restrict__ count,
              uint32_t *__restrict__ rank, double *__restrict__ wsums, unsigned *__restrict__ wmax) {
     using R = typename PosReal<DT>::type;
@@ -220,17 +224,17 @@ k_sort_count(const void *__restrict__ pos, const float *__restrict__ w,
     float mw = 0.0f;
     for (int64_t i = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const Obj<R> o = load_obj<DT>(pos, w, i, g);
+        const Obj<R> o = load_obj<DT>(pos, w, vals, i, g);
         int t3[3], cls;
         home_key<R>(o, g, t3, &cls);
         const int64_t key = kbase + (((int64_t)t3[0] * g.ntx + t3[1]) * g.ntx + t3[2]) * kClasses + cls;
         rank[i] = atomicAdd(count + key, 1u);
         if (WEIGHTED) {
-            const double wd = (double)o.w;
-            sw += wd;
-            sw2 += wd * wd;
-            swa += fabs(wd);
-            mw = fmaxf(mw, fabsf(o.w));
+            const double ad = (double)o.a;
+            sw += (double)o.w;
+            sw2 += ad * ad;
+            swa += fabs(ad);
+            mw = fmaxf(mw, fabsf(o.a));
         }
     }
     flush_wsums(sw, sw2, swa, mw, WEIGHTED, item, end - beg, wsums, wmax);
@@ -238,7 +242,7 @@ k_sort_count(const void *__restrict__ pos, const float *__restrict__ w,
 
 template <int DT>
 __global__ void __launch_bounds__(kCountThreads)
-k_sort_scatter(const void *__restrict__ pos, const float *__restrict__ w,
+k_sort_scatter(const void *__restrict__ pos, const float *__restrict__ w, const float *__restrict__ vals,
                const int64_t *__restrict__ item_off, PaintGeom g, const uint32_t *__restrict__ off,
                const uint32_t *__restrict__ rank, float4 *__restrict__ sorted, int *__restrict__ err) {
     using R = typename PosReal<DT>::type;
@@ -247,7 +251,7 @@ k_sort_scatter(const void *__restrict__ pos, const float *__restrict__ w,
     const int64_t kbase = (int64_t)item * g.ntiles * kClasses;
     for (int64_t i = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const Obj<R> o = load_obj<DT>(pos, w, i, g);
+        const Obj<R> o = load_obj<DT>(pos, w, vals, i, g);
         int t3[3], cls;
         home_key<R>(o, g, t3, &cls);
         const int64_t key = kbase + (((int64_t)t3[0] * g.ntx + t3[1]) * g.ntx + t3[2]) * kClasses + cls;
@@ -258,7 +262,7 @@ k_sort_scatter(const void *__restrict__ pos, const float *__restrict__ w,
         }
         sorted[dst] = make_float4((float)(o.s[0] - (R)(t3[0] * g.T)) + o.e[0],
                                   (float)(o.s[1] - (R)(t3[1] * g.T)) + o.e[1],
-                                  (float)(o.s[2] - (R)(t3[2] * g.T)) + o.e[2], o.w);
+                                  (float)(o.s[2] - (R)(t3[2] * g.T)) + o.e[2], o.a);
     }
 }
 
@@ -781,7 +785,7 @@ __device__ __forceinline__ void deposit_global(unsigned long long *__restrict__ 
 
 template <int DT, int P, int NM>
 __global__ void __launch_bounds__(kCountThreads)
-k_paint_atomic(const void *__restrict__ pos, const float *__restrict__ w,
+k_paint_atomic(const void *__restrict__ pos, const float *__restrict__ w, const float *__restrict__ vals,
                const int64_t *__restrict__ item_off, PaintGeom g, int S, bool weighted,
                unsigned long long *__restrict__ acc, double *__restrict__ wsums,
                unsigned *__restrict__ wmax) {
@@ -795,7 +799,7 @@ k_paint_atomic(const void *__restrict__ pos, const float *__restrict__ w,
     float mw = 0.0f;
     for (int64_t i = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const Obj<R> o = load_obj<DT>(pos, w, i, g);
+        const Obj<R> o = load_obj<DT>(pos, w, vals, i, g);
         int c0[3];
         float u[3];
 #pragma unroll
@@ -803,15 +807,15 @@ k_paint_atomic(const void *__restrict__ pos, const float *__restrict__ w,
             c0[a] = min((int)floor(o.s[a]), g.N - 1);
             u[a] = (float)(o.s[a] - (R)c0[a]) + o.e[a];
         }
-        const float ws = o.w * scale;
+        const float ws = o.a * scale;
 #pragma unroll
         for (int m = 0; m < NM; ++m) deposit_global<P>(ab + m * n3, g.N, c0, u, m ? 0.5f : 0.0f, ws);
         if (weighted) {
-            const double wd = (double)o.w;
-            sw += wd;
-            sw2 += wd * wd;
-            swa += fabs(wd);
-            mw = fmaxf(mw, fabsf(o.w));
+            const double ad = (double)o.a;
+            sw += (double)o.w;
+            sw2 += ad * ad;
+            swa += fabs(ad);
+            mw = fmaxf(mw, fabsf(o.a));
         }
     }
     flush_wsums(sw, sw2, swa, mw, weighted, item, end - beg, wsums, wmax);
@@ -895,11 +899,13 @@ struct BinSmem {
     __host__ __device__ static size_t bytes(const BinGeom &g) { return align_up(off_edge(g) + (size_t)g.nk * sizeof(int2), 16); }
 };
 
-template <bool IL, bool TWOD, bool POLES, typename R, typename C, typename A>
+// CROSS: the meshes of a second catalog at meshb; each mode contributes
+// Re(delta_a conj(delta_b)) instead of |delta|^2.
+template <bool IL, bool TWOD, bool POLES, typename R, typename C, typename A, bool CROSS = false>
 __global__ void __launch_bounds__(kBinThreads)
 k_bin(const C *__restrict__ mesh, long long item_stride_c, long long mesh_stride_c, int nchunks,
       BinGeom g, const R *__restrict__ cw, const C *__restrict__ ph, const int *__restrict__ kedge,
-      A *__restrict__ partial) {
+      A *__restrict__ partial, const C *__restrict__ meshb) {
     using SM = BinSmem<R, C, A>;
     extern __shared__ __align__(16) unsigned char smraw[];
     A *hist = reinterpret_cast<A *>(smraw);
@@ -917,6 +923,8 @@ k_bin(const C *__restrict__ mesh, long long item_stride_c, long long mesh_stride
     const int item = blockIdx.y;
     const C *m1 = mesh + (long long)item * item_stride_c;
     const C *m2 = m1 + mesh_stride_c;
+    const C *n1 = CROSS ? meshb : m1;
+    const C *n2 = n1 + mesh_stride_c;
     const long long CH = (long long)kBinThreads * kBinVec;
     const int half = g.N / 2;
     const int Nh = g.Nh;
@@ -966,9 +974,13 @@ k_bin(const C *__restrict__ mesh, long long item_stride_c, long long mesh_stride
                 const int mlast = r2 + (l + kBinVec - 1) * (l + kBinVec - 1);
                 if (r2 + l * l >= g.mhi || mlast < g.mlo) goto next_chunk;
             }
-            C a[kBinVec], b2[kBinVec];
+            C a[kBinVec], b2[kBinVec], ca[CROSS ? kBinVec : 1], cb2[CROSS && IL ? kBinVec : 1];
             load_vec(m1 + f0, a);
             if (IL) load_vec(m2 + f0, b2);
+            if (CROSS) {
+                load_vec(n1 + f0, ca);
+                if (IL) load_vec(n2 + f0, cb2);
+            }
             int cur2 = -1, cur1 = -1;                 // open register runs
             R run2 = (R)0, runm2 = (R)0, runm4 = (R)0;
 #pragma unroll
@@ -990,12 +1002,19 @@ k_bin(const C *__restrict__ mesh, long long item_stride_c, long long mesh_stride
                     while (b > 0 && m < e.x) e = sedge[--b];
                     while (b < g.nk - 1 && m >= e.y) e = sedge[++b];
                     C z = a[v];
+                    C y;
+                    if (CROSS) y = ca[CROSS ? v : 0];
                     if (IL) {
                         const C t = cmul(rowph, sph[l]);
                         z.x += b2[v].x * t.x - b2[v].y * t.y;
                         z.y += b2[v].x * t.y + b2[v].y * t.x;
+                        if (CROSS) {
+                            const C u = cb2[CROSS && IL ? v : 0];
+                            y.x += u.x * t.x - u.y * t.y;
+                            y.y += u.x * t.y + u.y * t.x;
+                        }
                     }
-                    R pw = (z.x * z.x + z.y * z.y) * rowcw * scw[l];
+                    R pw = (CROSS ? z.x * y.x + z.y * y.y : z.x * z.x + z.y * z.y) * rowcw * scw[l];
                     if (l != 0 && l != half) pw += pw;
                     int key = b;
                     if (TWOD) {
@@ -1072,17 +1091,25 @@ __global__ void k_bin_reduce(const A *__restrict__ partial, int G, int nh, int n
     sums2[((long long)item * nchunk + chunk) * nh + k] = s;
 }
 
+// Auto power of every catalog (cross_b < 0: block = catalog), or the cross
+// power of catalogs cross_a and cross_b (one block): normalization
+// L^3 / (sum w_a sum w_b), no shot noise; the result block then carries
+// sum w_a and sum w_b in its wsum and w2sum slots.
 __global__ void k_finalize(const double *__restrict__ sums2, int nchunk,
                            const unsigned long long *__restrict__ modes1d,
                            const unsigned long long *__restrict__ modes2d,
                            const double *__restrict__ wsums, const int *__restrict__ err,
-                           FinalGeom f, ResultLayout rl, double *__restrict__ res) {
+                           FinalGeom f, ResultLayout rl, double *__restrict__ res, int cross_a, int cross_b) {
+    const bool cross = cross_b >= 0;
     const int item = blockIdx.x;
+    const int ia = cross ? cross_a : item, ib = cross ? cross_b : item;
     const double *s0 = sums2 + (long long)item * nchunk * f.nh;
     double *r = res + (long long)item * f.RL;
-    const double wsum = wsums[4 * item], w2sum = wsums[4 * item + 1], wabs = wsums[4 * item + 2];
-    const double norm = f.L3 / (wsum * wsum);
-    const double shot = f.L3 * w2sum / (wsum * wsum);
+    const double wsum = wsums[4 * ia], wsum_b = wsums[4 * ib];
+    const double w2sum = cross ? wsum_b : wsums[4 * ia + 1];
+    const double wabs = fmax(wsums[4 * ia + 2], wsums[4 * ib + 2]);
+    const double norm = f.L3 / (wsum * wsum_b);
+    const double shot = cross ? 0.0 : f.L3 * w2sum / (wsum * wsum);
     const double sub = f.subtract_shot ? shot : 0.0;
     const double nan = __longlong_as_double(0x7ff8000000000000LL);
     auto S = [&](int k) {
@@ -1206,14 +1233,14 @@ ResultLayout result_layout(int nk, int nmu) {
 
 int paint_classes() { return kClasses; }
 
-cudaError_t launch_sort_count(const void *pos, int dtype, const float *w, const int64_t *item_off,
-                              int nitems, int64_t max_n, const PaintGeom &g, uint32_t *count,
-                              uint32_t *rank, double *wsums, unsigned *wmax, cudaStream_t st) {
+cudaError_t launch_sort_count(const void *pos, int dtype, const float *w, const float *vals,
+                              const int64_t *item_off, int nitems, int64_t max_n, const PaintGeom &g,
+                              uint32_t *count, uint32_t *rank, double *wsums, unsigned *wmax, cudaStream_t st) {
     dim3 grid(grid_for(max_n, kCountThreads, 1u << 20), nitems);
-    const bool weighted = w != nullptr || dtype == PK_F32X4;
+    const bool weighted = w != nullptr || vals != nullptr || dtype == PK_F32X4;
 #define PK_COUNT(DT)                                                                                    \
-    if (weighted) k_sort_count<DT, true><<<grid, kCountThreads, 0, st>>>(pos, w, item_off, g, count, rank, wsums, wmax); \
-    else k_sort_count<DT, false><<<grid, kCountThreads, 0, st>>>(pos, w, item_off, g, count, rank, wsums, wmax);
+    if (weighted) k_sort_count<DT, true><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, count, rank, wsums, wmax); \
+    else k_sort_count<DT, false><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, count, rank, wsums, wmax);
     switch (dtype) {
     case PK_F32: PK_COUNT(PK_F32) break;
     case PK_F64: PK_COUNT(PK_F64) break;
@@ -1223,14 +1250,15 @@ cudaError_t launch_sort_count(const void *pos, int dtype, const float *w, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_sort_scatter(const void *pos, int dtype, const float *w, const int64_t *item_off,
-                                int nitems, int64_t max_n, const PaintGeom &g, const uint32_t *off,
-                                const uint32_t *rank, float4 *sorted, int *err, cudaStream_t st) {
+cudaError_t launch_sort_scatter(const void *pos, int dtype, const float *w, const float *vals,
+                                const int64_t *item_off, int nitems, int64_t max_n, const PaintGeom &g,
+                                const uint32_t *off, const uint32_t *rank, float4 *sorted, int *err,
+                                cudaStream_t st) {
     dim3 grid(grid_for(max_n, kCountThreads, 1u << 20), nitems);
     switch (dtype) {
-    case PK_F32: k_sort_scatter<PK_F32><<<grid, kCountThreads, 0, st>>>(pos, w, item_off, g, off, rank, sorted, err); break;
-    case PK_F64: k_sort_scatter<PK_F64><<<grid, kCountThreads, 0, st>>>(pos, w, item_off, g, off, rank, sorted, err); break;
-    default: k_sort_scatter<PK_F32X4><<<grid, kCountThreads, 0, st>>>(pos, w, item_off, g, off, rank, sorted, err); break;
+    case PK_F32: k_sort_scatter<PK_F32><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, off, rank, sorted, err); break;
+    case PK_F64: k_sort_scatter<PK_F64><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, off, rank, sorted, err); break;
+    default: k_sort_scatter<PK_F32X4><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, off, rank, sorted, err); break;
     }
     return cudaGetLastError();
 }
@@ -1345,25 +1373,25 @@ cudaError_t launch_paint_tiles(const float4 *sorted, const uint32_t *off, int ni
 }
 
 template <int DT, int P, int NM>
-static cudaError_t atomic_inst(const void *pos, const float *w, const int64_t *item_off, int nitems,
+static cudaError_t atomic_inst(const void *pos, const float *w, const float *vals, const int64_t *item_off, int nitems,
                                int64_t max_n, const PaintGeom &g, int S, bool weighted,
                                unsigned long long *acc, double *wsums, unsigned *wmax, cudaStream_t st) {
     dim3 grid(grid_for(max_n, kCountThreads, 1u << 20), nitems);
-    k_paint_atomic<DT, P, NM><<<grid, kCountThreads, 0, st>>>(pos, w, item_off, g, S, weighted, acc,
+    k_paint_atomic<DT, P, NM><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, S, weighted, acc,
                                                              wsums, wmax);
     return cudaGetLastError();
 }
 
 template <int DT>
-static cudaError_t atomic_dispatch(const void *pos, const float *w, const int64_t *item_off, int nitems,
+static cudaError_t atomic_dispatch(const void *pos, const float *w, const float *vals, const int64_t *item_off, int nitems,
                                    int64_t max_n, const PaintGeom &g, int window, int nmesh, int S,
                                    bool weighted, unsigned long long *acc, double *wsums, unsigned *wmax,
                                    cudaStream_t st) {
 #define PK_ATOMIC_CASE(P)                                                                              \
     if (window == P)                                                                                   \
-        return nmesh == 2 ? atomic_inst<DT, P, 2>(pos, w, item_off, nitems, max_n, g, S, weighted, acc, \
+        return nmesh == 2 ? atomic_inst<DT, P, 2>(pos, w, vals, item_off, nitems, max_n, g, S, weighted, acc, \
                                                   wsums, wmax, st)                                    \
-                          : atomic_inst<DT, P, 1>(pos, w, item_off, nitems, max_n, g, S, weighted, acc, \
+                          : atomic_inst<DT, P, 1>(pos, w, vals, item_off, nitems, max_n, g, S, weighted, acc, \
                                                   wsums, wmax, st);
     PK_ATOMIC_CASE(2)
     PK_ATOMIC_CASE(3)
@@ -1372,20 +1400,20 @@ static cudaError_t atomic_dispatch(const void *pos, const float *w, const int64_
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_paint_atomic(const void *pos, int dtype, const float *w, const int64_t *item_off,
-                                int nitems, int64_t max_n, const PaintGeom &g, int window, int nmesh,
-                                int S, unsigned long long *acc, double *wsums, unsigned *wmax,
-                                cudaStream_t st) {
-    const bool weighted = w != nullptr || dtype == PK_F32X4;
+cudaError_t launch_paint_atomic(const void *pos, int dtype, const float *w, const float *vals,
+                                const int64_t *item_off, int nitems, int64_t max_n, const PaintGeom &g,
+                                int window, int nmesh, int S, unsigned long long *acc, double *wsums,
+                                unsigned *wmax, cudaStream_t st) {
+    const bool weighted = w != nullptr || vals != nullptr || dtype == PK_F32X4;
     switch (dtype) {
     case PK_F32:
-        return atomic_dispatch<PK_F32>(pos, w, item_off, nitems, max_n, g, window, nmesh, S, weighted, acc,
+        return atomic_dispatch<PK_F32>(pos, w, vals, item_off, nitems, max_n, g, window, nmesh, S, weighted, acc,
                                        wsums, wmax, st);
     case PK_F64:
-        return atomic_dispatch<PK_F64>(pos, w, item_off, nitems, max_n, g, window, nmesh, S, weighted, acc,
+        return atomic_dispatch<PK_F64>(pos, w, vals, item_off, nitems, max_n, g, window, nmesh, S, weighted, acc,
                                        wsums, wmax, st);
     default:
-        return atomic_dispatch<PK_F32X4>(pos, w, item_off, nitems, max_n, g, window, nmesh, S, weighted,
+        return atomic_dispatch<PK_F32X4>(pos, w, vals, item_off, nitems, max_n, g, window, nmesh, S, weighted,
                                          acc, wsums, wmax, st);
     }
 }
@@ -1415,12 +1443,12 @@ size_t bin_smem_bytes(const BinGeom &g, int f64) {
 
 int bin_threads() { return kBinThreads; }
 
-template <bool IL, bool TWOD, bool POLES, typename R, typename C, typename A>
+template <bool IL, bool TWOD, bool POLES, typename R, typename C, typename A, bool CROSS>
 static cudaError_t bin_inst(const void *mesh, long long item_stride_c, long long mesh_stride_c,
                             int nitems, int G, const BinGeom &g, const void *cw, const void *ph,
-                            const int *kedge, void *partial, cudaStream_t st) {
+                            const int *kedge, void *partial, const void *meshb, cudaStream_t st) {
     const size_t smem = BinSmem<R, C, A>::bytes(g);
-    auto kern = k_bin<IL, TWOD, POLES, R, C, A>;
+    auto kern = k_bin<IL, TWOD, POLES, R, C, A, CROSS>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     const long long CH = (long long)kBinThreads * kBinVec;
@@ -1429,25 +1457,27 @@ static cudaError_t bin_inst(const void *mesh, long long item_stride_c, long long
     kern<<<grid, kBinThreads, smem, st>>>(reinterpret_cast<const C *>(mesh), item_stride_c,
                                           mesh_stride_c, nchunks, g, reinterpret_cast<const R *>(cw),
                                           reinterpret_cast<const C *>(ph), kedge,
-                                          reinterpret_cast<A *>(partial));
+                                          reinterpret_cast<A *>(partial), reinterpret_cast<const C *>(meshb));
     return cudaGetLastError();
 }
 
-template <typename R, typename C, typename A>
+template <typename R, typename C, typename A, bool CROSS>
 static cudaError_t bin_dispatch(const void *mesh, int il, long long is, long long ms, int nitems,
                                 int G, const BinGeom &g, const void *cw, const void *ph,
-                                const int *kedge, void *partial, cudaStream_t st) {
+                                const int *kedge, void *partial, const void *meshb, cudaStream_t st) {
     const int key = (il ? 4 : 0) | (g.twod ? 2 : 0) | (g.poles ? 1 : 0);
+#define PK_BIN(a, b, c) bin_inst<a, b, c, R, C, A, CROSS>(mesh, is, ms, nitems, G, g, cw, ph, kedge, partial, meshb, st)
     switch (key) {
-    case 0: return bin_inst<false, false, false, R, C, A>(mesh, is, ms, nitems, G, g, cw, ph, kedge, partial, st);
-    case 1: return bin_inst<false, false, true, R, C, A>(mesh, is, ms, nitems, G, g, cw, ph, kedge, partial, st);
-    case 2: return bin_inst<false, true, false, R, C, A>(mesh, is, ms, nitems, G, g, cw, ph, kedge, partial, st);
-    case 3: return bin_inst<false, true, true, R, C, A>(mesh, is, ms, nitems, G, g, cw, ph, kedge, partial, st);
-    case 4: return bin_inst<true, false, false, R, C, A>(mesh, is, ms, nitems, G, g, cw, ph, kedge, partial, st);
-    case 5: return bin_inst<true, false, true, R, C, A>(mesh, is, ms, nitems, G, g, cw, ph, kedge, partial, st);
-    case 6: return bin_inst<true, true, false, R, C, A>(mesh, is, ms, nitems, G, g, cw, ph, kedge, partial, st);
-    default: return bin_inst<true, true, true, R, C, A>(mesh, is, ms, nitems, G, g, cw, ph, kedge, partial, st);
+    case 0: return PK_BIN(false, false, false);
+    case 1: return PK_BIN(false, false, true);
+    case 2: return PK_BIN(false, true, false);
+    case 3: return PK_BIN(false, true, true);
+    case 4: return PK_BIN(true, false, false);
+    case 5: return PK_BIN(true, false, true);
+    case 6: return PK_BIN(true, true, false);
+    default: return PK_BIN(true, true, true);
     }
+#undef PK_BIN
 }
 
 cudaError_t launch_bin(const void *mesh, int f64, int interlaced, long long item_stride_c,
@@ -1455,10 +1485,21 @@ cudaError_t launch_bin(const void *mesh, int f64, int interlaced, long long item
                        const BinGeom &g, const void *cw, const void *ph, const int *kedge,
                        void *partial, cudaStream_t st) {
     if (f64)
-        return bin_dispatch<double, double2, double>(mesh, interlaced, item_stride_c, mesh_stride_c,
-                                                      nitems, ctas_per_item, g, cw, ph, kedge, partial, st);
-    return bin_dispatch<float, float2, float>(mesh, interlaced, item_stride_c, mesh_stride_c, nitems,
-                                              ctas_per_item, g, cw, ph, kedge, partial, st);
+        return bin_dispatch<double, double2, double, false>(mesh, interlaced, item_stride_c, mesh_stride_c,
+                                                             nitems, ctas_per_item, g, cw, ph, kedge, partial,
+                                                             nullptr, st);
+    return bin_dispatch<float, float2, float, false>(mesh, interlaced, item_stride_c, mesh_stride_c, nitems,
+                                                     ctas_per_item, g, cw, ph, kedge, partial, nullptr, st);
+}
+
+cudaError_t launch_bin_cross(const void *mesh_a, const void *mesh_b, int f64, int interlaced,
+                             long long mesh_stride_c, int ctas, const BinGeom &g, const void *cw,
+                             const void *ph, const int *kedge, void *partial, cudaStream_t st) {
+    if (f64)
+        return bin_dispatch<double, double2, double, true>(mesh_a, interlaced, 0, mesh_stride_c, 1, ctas, g, cw,
+                                                            ph, kedge, partial, mesh_b, st);
+    return bin_dispatch<float, float2, float, true>(mesh_a, interlaced, 0, mesh_stride_c, 1, ctas, g, cw, ph,
+                                                    kedge, partial, mesh_b, st);
 }
 
 int bin_ctas_per_sm(const BinGeom &g, int f64) {
@@ -1493,7 +1534,16 @@ cudaError_t launch_finalize(const double *sums2, int G, const unsigned long long
                             const unsigned long long *modes2d, const double *wsums, const int *err,
                             const FinalGeom &f, int nitems, double *res, cudaStream_t st) {
     const ResultLayout rl = result_layout(f.nk, f.nmu);
-    k_finalize<<<nitems, 256, 0, st>>>(sums2, reduce_chunks(G), modes1d, modes2d, wsums, err, f, rl, res);
+    k_finalize<<<nitems, 256, 0, st>>>(sums2, reduce_chunks(G), modes1d, modes2d, wsums, err, f, rl, res, -1, -1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_cross(const double *sums2, int G, const unsigned long long *modes1d,
+                                  const unsigned long long *modes2d, const double *wsums, const int *err,
+                                  const FinalGeom &f, int item_a, int item_b, double *res, cudaStream_t st) {
+    const ResultLayout rl = result_layout(f.nk, f.nmu);
+    k_finalize<<<1, 256, 0, st>>>(sums2, reduce_chunks(G), modes1d, modes2d, wsums, err, f, rl, res, item_a,
+                                  item_b);
     return cudaGetLastError();
 }
 
