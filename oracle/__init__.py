@@ -375,3 +375,49 @@ def lognormal_catalog(n: int, box_size: float, ng: int, seed: int, slope: float 
     G, gk, _ = linear_field(ng, box_size, slope, seed, amp, variance)
     psi = displacement_z(gk, box_size) if f_rsd else None
     return place(lognormal_weights(G), box_size, psi, f_rsd, seed, n)
+
+
+def projected_power(pos, weights, box_size, nmesh, window="cic", interlaced=False, compensated=True,
+                    dk=None, kmin=0.0, kmax=None, axes=(0, 1), subtract_shot=True):
+    """Power spectrum of the painted field projected onto `axes` (summed over
+    the other axes; the ProjectedFFTPower of Sec. 3.4.1), FP64: the projected
+    field's d-dimensional FFT (d = len(axes)), the interlacing combine and
+    the compensation over the kept axes, delta = F~ / sum w, P = L^d |delta|^2
+    per mode (every mode of the full d-dimensional grid counted once), binned
+    in |k| with the FFTPower k bins; shot noise L^d sum w^2 / (sum w)^2."""
+    axes = tuple(sorted(int(a) for a in axes))
+    d = len(axes)
+    drop = tuple(a for a in range(3) if a not in axes)
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    w = np.ones(pos.shape[0]) if weights is None else np.asarray(weights, dtype=np.float64)
+    wsum, w2sum = float(np.sum(w)), float(np.sum(w * w))
+    T = np.fft.fftn(paint(pos, weights, box_size, nmesh, window, 0.0).sum(axis=drop))
+    n1 = np.fft.fftfreq(nmesh, 1.0 / nmesh)
+    grids = np.meshgrid(*([n1] * d), indexing="ij")
+    if interlaced:
+        T2 = np.fft.fftn(paint(pos, weights, box_size, nmesh, window, 0.5).sum(axis=drop))
+        T = 0.5 * (T + T2 * np.exp(1j * np.pi * sum(grids) / nmesh))
+    if compensated:
+        W = np.ones_like(grids[0])
+        for g in grids:
+            W = W * np.sinc(g / nmesh) ** _order(window)
+        T = T / W
+    delta = T / wsum
+    P = box_size ** d * np.abs(delta) ** 2
+    m = sum(g.astype(np.int64) ** 2 for g in grids).astype(np.int64)
+    nk = nbins(box_size, nmesh, dk, kmin, kmax)
+    b = np.full(m.shape, -1, np.int64)
+    for mv in np.unique(m):
+        if mv > 0:
+            b[m == mv] = kbin(int(mv), box_size, kmin, dk)
+    ok = (m > 0) & (b >= 0) & (b < nk)
+    kF = 2.0 * math.pi / box_size
+    modes = np.bincount(b[ok], minlength=nk).astype(np.int64)
+    ksum = np.bincount(b[ok], weights=kF * np.sqrt(m[ok].astype(np.float64)), minlength=nk)
+    psum = np.bincount(b[ok], weights=P[ok], minlength=nk)
+    shot = box_size ** d * w2sum / wsum ** 2
+    with np.errstate(invalid="ignore", divide="ignore"):
+        res = {"k": ksum / modes, "modes": modes, "power_raw": psum / modes,
+               "power": psum / modes - (shot if subtract_shot else 0.0), "shot_noise": shot, "nk": nk,
+               "wsum": wsum, "w2sum": w2sum}
+    return res
