@@ -218,6 +218,32 @@ pk_status pk_cross(pk_plan_t plan, int item_a, int item_b);
  * pk_destroy.  Errors: PK_ESTATE (no pk_cross yet), PK_EOVERFLOW, PK_ECUDA. */
 pk_status pk_cross_result(pk_plan_t plan, pk_result_view *out);
 
+/* Power spectrum of the field projected onto one or two axes (the
+ * ProjectedFFTPower of Sec. 3.4.1, e.g. for Lyman-alpha or lensing-like
+ * projected fields).  The painted field summed over the dropped axes has, by
+ * the projection-slice theorem, the transform of the 3D field at index 0 along
+ * them, so the plan's transform of catalog `item` (after pk_compute) already
+ * holds it.  Each mode of that plane or line: interlacing combine and
+ * compensation as in pk_compute, P = L^d |F~|^2 / (sum w)^2 with d the number
+ * of kept axes, every mode of the full d-dimensional grid counted once, binned
+ * in |k| with the plan's k bins; the shot noise L^d sum w^2 / (sum w)^2 is
+ * subtracted if the plan's subtract_shot is set.  keep_axes: bit 0 x, bit 1 y,
+ * bit 2 z; one or two bits.  The call waits for the result; the pointers in
+ * *out stay valid until the next pk_projected or pk_destroy.
+ * Errors: PK_EINVAL (keep_axes, item), PK_ESTATE (no pk_compute since the last
+ * paint), PK_ECUDA. */
+typedef struct {
+    int nk, ndim;                 /* k bins; d = number of kept axes               */
+    const double *k_edges;        /* nk + 1                                       */
+    const double *k_mean;         /* nk: mean |k| of the bin's modes              */
+    const double *pk;             /* nk: projected power                          */
+    const uint64_t *modes;        /* nk: modes of the d-dimensional grid          */
+    double shot_noise;            /* L^d sum(w^2) / sum(w)^2                      */
+    double wsum;                  /* sum(w)                                       */
+} pk_projected_view;
+
+pk_status pk_projected(pk_plan_t plan, int item, unsigned keep_axes, pk_projected_view *out);
+
 /* Copy painted mesh `mesh` (0, or 1 = the interlaced mesh) of catalog `item`
  * into dst as a dense N x N x N array (z fastest) of the plan's precision
  * (float for PK_MESH_F32, double for PK_MESH_F64): the painted field F of

@@ -42,7 +42,7 @@ WINDOWS = {"cic": PK_CIC, "tsc": PK_TSC, "pcs": PK_PCS}
 EXPORTED = ["pk_config_default", "pk_plan", "pk_paint", "pk_paint_many", "pk_compute",
             "pk_result", "pk_mesh", "pk_destroy", "pk_status_string", "pk_last_error",
             "pk_plan_error", "pk_enable_timing", "pk_stage_times", "pk_launch_count",
-            "pk_bin_static", "pk_cross", "pk_cross_result", "pk_paint_values", "pk_lognormal_plan", "pk_lognormal_field", "pk_lognormal_draw",
+            "pk_bin_static", "pk_cross", "pk_cross_result", "pk_paint_values", "pk_projected", "pk_lognormal_plan", "pk_lognormal_field", "pk_lognormal_draw",
             "pk_lognormal_amp", "pk_lognormal_launch_count", "pk_lognormal_error", "pk_lognormal_destroy"]
 STAGES = ["sort", "paint", "fft", "bin", "final"]
 
@@ -75,6 +75,13 @@ class pk_result_view(ctypes.Structure):
         ("k_edges", _dp), ("mu_edges", _dp), ("k_mean", _dp), ("pk", _dp), ("poles", _dp),
         ("modes", _up), ("k_mean2d", _dp), ("mu_mean2d", _dp), ("pkmu", _dp), ("modes2d", _up),
         ("shot_noise", ctypes.c_double), ("wsum", ctypes.c_double), ("w2sum", ctypes.c_double),
+    ]
+
+
+class pk_projected_view(ctypes.Structure):
+    _fields_ = [
+        ("nk", ctypes.c_int), ("ndim", ctypes.c_int), ("k_edges", _dp), ("k_mean", _dp), ("pk", _dp),
+        ("modes", _up), ("shot_noise", ctypes.c_double), ("wsum", ctypes.c_double),
     ]
 
 
@@ -113,6 +120,8 @@ def load():
         lib.pk_cross.restype = i
         lib.pk_cross_result.argtypes = [vp, ctypes.POINTER(pk_result_view)]
         lib.pk_cross_result.restype = i
+        lib.pk_projected.argtypes = [vp, i, ctypes.c_uint, ctypes.POINTER(pk_projected_view)]
+        lib.pk_projected.restype = i
         lib.pk_mesh.argtypes = [vp, i, i, vp]
         lib.pk_mesh.restype = i
         lib.pk_destroy.argtypes = [vp]
@@ -326,6 +335,22 @@ def pk_cross(plan, item_a, item_b) -> dict:
     v = pk_result_view()
     _check(load().pk_cross_result(plan, ctypes.byref(v)), plan)
     return _view_dict(v)
+
+
+AXES = {"x": 1, "y": 2, "z": 4}
+
+
+def pk_projected(plan, item=0, axes=(0, 1)) -> dict:
+    """Power of catalog ``item`` projected onto ``axes`` (indices 0-2 or
+    names "x", "y", "z"; one or two axes), after pk_compute."""
+    mask = 0
+    for a in axes:
+        mask |= AXES[a] if isinstance(a, str) else (1 << int(a))
+    v = pk_projected_view()
+    _check(load().pk_projected(plan, int(item), mask, ctypes.byref(v)), plan)
+    return {"nk": v.nk, "ndim": v.ndim, "k_edges": _arr(v.k_edges, v.nk + 1), "k": _arr(v.k_mean, v.nk),
+            "power": _arr(v.pk, v.nk), "modes": _arr(v.modes, v.nk, np.int64), "shot_noise": v.shot_noise,
+            "wsum": v.wsum}
 
 
 def pk_mesh(plan, item, mesh, nmesh, f64=False):

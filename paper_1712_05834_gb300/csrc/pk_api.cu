@@ -70,6 +70,9 @@ struct pk_plan_s {
     void *d_partial = nullptr;
     double *d_sums2 = nullptr, *d_res = nullptr, *h_res = nullptr;
     double *d_xres = nullptr, *h_xres = nullptr;   // cross-power result block
+    double *d_proj = nullptr;                      // projected power: 3 sums per k bin
+    std::vector<double> proj_k, proj_pk;
+    std::vector<uint64_t> proj_modes;
     cudaEvent_t xdone = nullptr;
     int xdone_valid = 0, xcomputed = 0;
     unsigned long long *d_modes1d = nullptr, *d_modes2d = nullptr;
@@ -130,7 +133,7 @@ void free_plan(pk_plan_s *p) {
     void *dev[] = {p->mesh, p->d_count, p->d_off, p->d_scan_tmp, p->d_rank, p->d_sorted,
                    p->d_stage, p->d_item_off, p->d_wsums, p->d_wmax, p->d_cw, p->d_ph,
                    p->d_kedge, p->d_partial, p->d_sums2, p->d_res, p->d_modes1d, p->d_modes2d,
-                   p->d_err, p->d_acc, p->fft_work, p->d_xres};
+                   p->d_err, p->d_acc, p->fft_work, p->d_xres, p->d_proj};
     for (void *d : dev)
         if (d) cudaFree(d);
     if (p->h_res) cudaFreeHost(p->h_res);
@@ -385,6 +388,7 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
     PK_CUDA(P, dev_alloc(&P->d_res, sizeof(double) * (size_t)P->B * fg.RL));
     PK_CUDA(P, cudaMallocHost(reinterpret_cast<void **>(&P->h_res), sizeof(double) * (size_t)P->B * fg.RL));
     PK_CUDA(P, dev_alloc(&P->d_xres, sizeof(double) * (size_t)fg.RL));
+    PK_CUDA(P, dev_alloc(&P->d_proj, sizeof(double) * 3 * (size_t)nk));
     PK_CUDA(P, cudaMallocHost(reinterpret_cast<void **>(&P->h_xres), sizeof(double) * (size_t)fg.RL));
     PK_CUDA(P, cudaEventCreateWithFlags(&P->xdone, cudaEventDisableTiming));
     const int nq = nmu > 0 ? nmu : 1;
@@ -792,6 +796,58 @@ pk_status pk_cross_result(pk_plan_t P, pk_result_view *out) {
     if (!P->xcomputed) return fail(P, PK_ESTATE, "no pk_cross yet");
     if (P->xdone_valid) PK_CUDA(P, cudaEventSynchronize(P->xdone));
     return fill_view(P, P->h_xres, out);
+}
+
+pk_status pk_projected(pk_plan_t P, int item, unsigned keep_axes, pk_projected_view *out) {
+    if (!P) return PK_EINVAL;
+    P->err.clear();
+    if (!out) return fail(P, PK_EINVAL, "out is NULL");
+    const int d = (int)((keep_axes & 1u) + ((keep_axes >> 1) & 1u) + ((keep_axes >> 2) & 1u));
+    if ((keep_axes & ~7u) != 0 || d < 1 || d > 2)
+        return fail(P, PK_EINVAL, "keep_axes must name one or two of the axes x (1), y (2), z (4)");
+    if (!P->transformed || P->computed < 1) return fail(P, PK_ESTATE, "pk_projected needs a pk_compute first");
+    if (item < 0 || item >= P->computed) return fail(P, PK_EINVAL, "item out of range");
+    const cudaStream_t st = P->st;
+    const int nk = P->bg.nk;
+    const size_t csz = 2 * P->esz;
+    const size_t item_bytes = (size_t)P->nm * P->mesh_reals * P->esz;
+    const char *m1 = reinterpret_cast<const char *>(P->mesh) + (size_t)item * item_bytes;
+    const char *m2 = P->cfg.interlaced ? m1 + (size_t)(P->mesh_reals / 2) * csz : nullptr;
+    PK_CUDA(P, cudaMemsetAsync(P->d_proj, 0, sizeof(double) * 3 * (size_t)nk, st));
+    PK_CUDA(P, launch_plane_bin(m1, m2, P->f64, P->N, (int)keep_axes, P->d_cw, P->d_ph, P->d_kedge, nk, P->kF,
+                                P->d_proj, P->nsm, st));
+    P->launches += 1;
+    std::vector<double> sums(3 * (size_t)nk);
+    double ws[4];
+    PK_CUDA(P, cudaMemcpyAsync(sums.data(), P->d_proj, sizeof(double) * sums.size(), cudaMemcpyDeviceToHost, st));
+    PK_CUDA(P, cudaMemcpyAsync(ws, P->d_wsums + 4 * item, sizeof(ws), cudaMemcpyDeviceToHost, st));
+    PK_CUDA(P, cudaStreamSynchronize(st));
+    const double L = P->cfg.box_size;
+    const double Ld = d == 1 ? L : L * L;
+    const double wsum = ws[0], w2sum = ws[1];
+    const double norm = Ld / (wsum * wsum);
+    const double shot = Ld * w2sum / (wsum * wsum);
+    P->proj_k.assign(nk, NAN);
+    P->proj_pk.assign(nk, NAN);
+    P->proj_modes.assign(nk, 0);
+    for (int b = 0; b < nk; ++b) {
+        const double cnt = sums[3 * b];
+        P->proj_modes[b] = (uint64_t)cnt;
+        if (cnt > 0.0) {
+            P->proj_k[b] = sums[3 * b + 1] / cnt;
+            P->proj_pk[b] = norm * sums[3 * b + 2] / cnt - (P->cfg.subtract_shot ? shot : 0.0);
+        }
+    }
+    memset(out, 0, sizeof(*out));
+    out->nk = nk;
+    out->ndim = d;
+    out->k_edges = P->k_edges.data();
+    out->k_mean = P->proj_k.data();
+    out->pk = P->proj_pk.data();
+    out->modes = P->proj_modes.data();
+    out->shot_noise = shot;
+    out->wsum = wsum;
+    return PK_OK;
 }
 
 static pk_status fill_view(pk_plan_s *P, const double *r, pk_result_view *out) {

@@ -116,6 +116,12 @@ cudaError_t launch_finalize_cross(const double *sums2, int G, const unsigned lon
                                   const unsigned long long *modes2d, const double *wsums, const int *err,
                                   const FinalGeom &f, int item_a, int item_b, double *res, cudaStream_t st);
 
+// Projected power: bin the plane / line of one catalog's transform that keeps
+// the axes in keep_mask (bit a: axis a); sums[3 b + {0,1,2}] += h, h k, h |F|^2 cw.
+cudaError_t launch_plane_bin(const void *m1, const void *m2, int f64, int N, int keep_mask, const void *cw,
+                             const void *ph, const int *kedge, int nk, double kF, double *sums, int nsm,
+                             cudaStream_t st);
+
 cudaError_t launch_geom_hist(const BinGeom &g, unsigned long long *H, unsigned long long *HL,
                              cudaStream_t st);
 cudaError_t launch_geom_finalize(const BinGeom &g, const int *kedge, double kF,

@@ -1153,6 +1153,57 @@ __global__ void k_finalize(const double *__restrict__ sums2, int nchunk,
     }
 }
 
+// ---- projected power (ProjectedFFTPower): one plane or line of the transform ----
+// By the projection-slice theorem the d-dimensional transform of the field
+// summed over the dropped axes is the 3D transform at index 0 along them, so
+// the projected power needs only those modes.  Each mode of the plane: the
+// usual interlacing combine and compensation, |delta|^2 (times the half-grid
+// weight h when z is kept), exact k bin from the m-edge table, FP64 atomics
+// into count / sum h k / sum h |F|^2 cw per bin.
+template <typename R, typename C>
+__global__ void k_plane_bin(const C *__restrict__ m1, const C *__restrict__ m2, int N, int keep_mask,
+                            const R *__restrict__ cw, const C *__restrict__ ph, const int *__restrict__ kedge,
+                            int nk, double kF, double *__restrict__ sums) {
+    const int Nh = N / 2 + 1;
+    const int nx = (keep_mask & 1) ? N : 1, ny = (keep_mask & 2) ? N : 1, nz = (keep_mask & 4) ? Nh : 1;
+    const long long total = (long long)nx * ny * nz;
+    const int half = N / 2;
+    for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < total;
+         f += (long long)gridDim.x * blockDim.x) {
+        const int l = (int)(f % nz);
+        const long long r = f / nz;
+        const int j = (int)(r % ny);
+        const int i = (int)(r / ny);
+        const int ip = i < half ? i : i - N, jp = j < half ? j : j - N;
+        const long long m = (long long)ip * ip + (long long)jp * jp + (long long)l * l;
+        if (m == 0 || m < kedge[0] || m >= kedge[nk]) continue;
+        int a = 0, b = nk;                               // kedge[a] <= m < kedge[b]
+        while (b - a > 1) {
+            const int mid = (a + b) >> 1;
+            if (kedge[mid] <= m) a = mid;
+            else b = mid;
+        }
+        const long long idx = ((long long)i * N + j) * Nh + l;
+        double zr = (double)m1[idx].x, zi = (double)m1[idx].y;
+        double wgt = (double)cw[i] * (double)cw[j] * (double)cw[l];
+        if (m2) {
+            // e^{+i pi (i' + j' + l) / N} as the product of the per-axis phase table entries
+            const C pa = ph[ip + half], pb = ph[jp + half], pc = ph[l + half];
+            const double tr = (double)pa.x * pb.x - (double)pa.y * pb.y;
+            const double ti = (double)pa.x * pb.y + (double)pa.y * pb.x;
+            const double er = tr * pc.x - ti * pc.y, ei = tr * pc.y + ti * pc.x;
+            const double br = (double)m2[idx].x, bi = (double)m2[idx].y;
+            zr += br * er - bi * ei;
+            zi += br * ei + bi * er;
+            wgt *= 0.25;
+        }
+        const double h = ((keep_mask & 4) && l != 0 && l != half) ? 2.0 : 1.0;
+        atomicAdd(sums + 3 * a, h);
+        atomicAdd(sums + 3 * a + 1, h * kF * sqrt((double)m));
+        atomicAdd(sums + 3 * a + 2, h * (zr * zr + zi * zi) * wgt);
+    }
+}
+
 // ---- plan-time geometry: integer histograms over (m, q) ----
 __global__ void k_geom_hist(BinGeom g, unsigned long long *__restrict__ H,
                             unsigned long long *__restrict__ HL) {
@@ -1544,6 +1595,23 @@ cudaError_t launch_finalize_cross(const double *sums2, int G, const unsigned lon
     const ResultLayout rl = result_layout(f.nk, f.nmu);
     k_finalize<<<1, 256, 0, st>>>(sums2, reduce_chunks(G), modes1d, modes2d, wsums, err, f, rl, res, item_a,
                                   item_b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plane_bin(const void *m1, const void *m2, int f64, int N, int keep_mask, const void *cw,
+                             const void *ph, const int *kedge, int nk, double kF, double *sums, int nsm,
+                             cudaStream_t st) {
+    const int Nh = N / 2 + 1;
+    const long long total = (long long)((keep_mask & 1) ? N : 1) * ((keep_mask & 2) ? N : 1) * ((keep_mask & 4) ? Nh : 1);
+    const unsigned grid = grid_for(total, 256, (unsigned)(nsm > 0 ? nsm * 8 : 1024));
+    if (f64)
+        k_plane_bin<double, double2><<<grid, 256, 0, st>>>(
+            reinterpret_cast<const double2 *>(m1), reinterpret_cast<const double2 *>(m2), N, keep_mask,
+            reinterpret_cast<const double *>(cw), reinterpret_cast<const double2 *>(ph), kedge, nk, kF, sums);
+    else
+        k_plane_bin<float, float2><<<grid, 256, 0, st>>>(
+            reinterpret_cast<const float2 *>(m1), reinterpret_cast<const float2 *>(m2), N, keep_mask,
+            reinterpret_cast<const float *>(cw), reinterpret_cast<const float2 *>(ph), kedge, nk, kF, sums);
     return cudaGetLastError();
 }
 

@@ -97,7 +97,7 @@ def _c_layout(tmp_path, struct, fields):
     return int(out[0]), [int(v) for v in out[1:]]
 
 
-@pytest.mark.parametrize("name", ["pk_config", "pk_result_view", "pk_lognormal_config"])
+@pytest.mark.parametrize("name", ["pk_config", "pk_result_view", "pk_lognormal_config", "pk_projected_view"])
 def test_ctypes_structs_match_the_header(pk, tmp_path, name):
     cls = getattr(pk, name)
     fields = [f for f, _ in cls._fields_]
