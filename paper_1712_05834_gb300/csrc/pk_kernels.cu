@@ -477,23 +477,27 @@ __device__ __forceinline__ int seg_dx(int s) { const int ax = s / 15; return ax 
 __device__ __forceinline__ int seg_dy(int s) { const int ay = (s / 3) % 5; return ay == 0 ? -1 : (ay == 4 ? 1 : 0); }
 __device__ __forceinline__ int seg_dz(int s) { return s % 3 - 1; }
 
-// Copy candidates [k0, k0 + n) of the tile into shared memory, already in this
-// tile's frame (segment shift added) and with the weight scaled by 2^S.
+// Candidate k of the tile (k < s_pre[kSegments]) in this tile's frame
+// (segment shift added), weight scaled by 2^S.
+__device__ __forceinline__ float4 fetch_candidate(const float4 *__restrict__ sorted, const uint32_t *s_beg,
+                                                  const uint32_t *s_pre, int T, uint32_t k, float scale) {
+    int lo_s = 0, hi_s = kSegments;                   // s_pre[lo_s] <= k < s_pre[hi_s]
+    while (hi_s - lo_s > 1) {
+        const int mid = (lo_s + hi_s) >> 1;
+        if (s_pre[mid] <= k) lo_s = mid;
+        else hi_s = mid;
+    }
+    const float4 v = __ldg(sorted + s_beg[lo_s] + (k - s_pre[lo_s]));
+    return make_float4(v.x + (float)(seg_dx(lo_s) * T), v.y + (float)(seg_dy(lo_s) * T),
+                       v.z + (float)(seg_dz(lo_s) * T), v.w * scale);
+}
+
+// Copy candidates [k0, k0 + n) of the tile into shared memory.
 __device__ __forceinline__ void stage_candidates(const float4 *__restrict__ sorted, const uint32_t *s_beg,
                                                  const uint32_t *s_pre, int T, uint32_t k0, uint32_t n,
                                                  float scale, float4 *cand) {
-    for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
-        const uint32_t k = k0 + j;
-        int lo_s = 0, hi_s = kSegments;               // s_pre[lo_s] <= k < s_pre[hi_s]
-        while (hi_s - lo_s > 1) {
-            const int mid = (lo_s + hi_s) >> 1;
-            if (s_pre[mid] <= k) lo_s = mid;
-            else hi_s = mid;
-        }
-        const float4 v = __ldg(sorted + s_beg[lo_s] + (k - s_pre[lo_s]));
-        cand[j] = make_float4(v.x + (float)(seg_dx(lo_s) * T), v.y + (float)(seg_dy(lo_s) * T),
-                              v.z + (float)(seg_dz(lo_s) * T), v.w * scale);
-    }
+    for (uint32_t j = threadIdx.x; j < n; j += blockDim.x)
+        cand[j] = fetch_candidate(sorted, s_beg, s_pre, T, k0 + j, scale);
 }
 
 template <int P, int MODE, int TC>
@@ -511,18 +515,6 @@ __device__ __forceinline__ void deposit_any(const float4 *cand, uint32_t n, unsi
     if (sp.fast == 2) deposit_staged<P, 2, TC>(cand, n, lo, hi, acc64, sp, T, sh);
     else if (sp.fast == 1) deposit_staged<P, 1, TC>(cand, n, lo, hi, acc64, sp, T, sh);
     else deposit_staged<P, 0, TC>(cand, n, lo, hi, acc64, sp, T, sh);
-}
-
-// Both meshes of an interlaced pair in one sweep over the candidates (MODE 2
-// only: the hi words of the split are free and hold mesh 1).
-template <int P, int TC>
-__device__ __forceinline__ void deposit_both(const float4 *cand, uint32_t n, unsigned *lo0, unsigned *lo1,
-                                             const Split &sp, int T) {
-    for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
-        const float4 v = cand[j];
-        deposit<P, 2, TC>(lo0, nullptr, nullptr, sp, T, v.x, v.y, v.z, v.w);
-        deposit<P, 2, TC>(lo1, nullptr, nullptr, sp, T, v.x + 0.5f, v.y + 0.5f, v.z + 0.5f, v.w);
-    }
 }
 
 // Write one tile's cells to the mesh (r2c layout, rows of T cells along z at
@@ -690,14 +682,15 @@ k_paint_tiles(const float4 *__restrict__ sorted, const uint32_t *__restrict__ of
     }
     const float scale = ldexpf(1.0f, S);
     const float inv_scale = ldexpf(1.0f, -S);
+    // With no split needed (unit weights, sparse tile) both meshes of an
+    // interlaced pair are painted in one sweep: mesh 0 into lo, mesh 1 into hi,
+    // each candidate read once straight from the sorted copy (nothing to stage).
+    const bool both = NM == 2 && sp.fast == 2;
     const bool staged_once = total <= (uint32_t)kStage;
-    if (staged_once) stage_candidates(sorted, s_beg, s_pre, T, 0u, total, scale, cand);
+    if (staged_once && !both) stage_candidates(sorted, s_beg, s_pre, T, 0u, total, scale, cand);
     const long long pitch = 2LL * (g.N / 2 + 1);
     M *base = mesh + item * item_stride;
 
-    // With no split needed (unit weights, sparse tile) both meshes of an
-    // interlaced pair are painted in one pass: mesh 0 into lo, mesh 1 into hi.
-    const bool both = NM == 2 && sp.fast == 2;
     const int passes = both ? 1 : NM;
     const long long tile_off = ((long long)tx * T * g.N + (long long)ty * T) * pitch + (long long)tz * T;
 #pragma unroll 1
@@ -710,17 +703,21 @@ k_paint_tiles(const float4 *__restrict__ sorted, const uint32_t *__restrict__ of
         }
         __syncthreads();
         const float sh = m ? 0.5f : 0.0f;
-        if (staged_once) {
-            if (both) deposit_both<P, TC>(cand, total, lo, hi, sp, T);
-            else deposit_any<P, TC>(cand, total, lo, hi, acc64, sp, T, sh);
+        if (both) {
+            for (uint32_t k = threadIdx.x; k < total; k += blockDim.x) {
+                const float4 v = fetch_candidate(sorted, s_beg, s_pre, T, k, scale);
+                deposit<P, 2, TC>(lo, nullptr, nullptr, sp, T, v.x, v.y, v.z, v.w);
+                deposit<P, 2, TC>(hi, nullptr, nullptr, sp, T, v.x + 0.5f, v.y + 0.5f, v.z + 0.5f, v.w);
+            }
+        } else if (staged_once) {
+            deposit_any<P, TC>(cand, total, lo, hi, acc64, sp, T, sh);
         } else {
             for (uint32_t k0 = 0; k0 < total; k0 += kStage) {     // dense tile: batches
                 const uint32_t n = min((uint32_t)kStage, total - k0);
                 __syncthreads();                                  // previous batch consumed
                 stage_candidates(sorted, s_beg, s_pre, T, k0, n, scale, cand);
                 __syncthreads();
-                if (both) deposit_both<P, TC>(cand, n, lo, hi, sp, T);
-                else deposit_any<P, TC>(cand, n, lo, hi, acc64, sp, T, sh);
+                deposit_any<P, TC>(cand, n, lo, hi, acc64, sp, T, sh);
             }
         }
         __syncthreads();
