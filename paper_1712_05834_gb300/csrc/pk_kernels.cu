@@ -1045,9 +1045,15 @@ k_bin(const C *__restrict__ mesh, long long item_stride_c, long long mesh_stride
                             runm2 = (R)0;
                             runm4 = (R)0;
                         }
+                        // FP32: mu = l rsqrt(m) from the k-bin estimate (a few ulp);
+                        // FP64: the exact quotient
                         R mu2;
-                        if (sizeof(R) == 4) mu2 = (R)__fdividef((float)(l * l), (float)m);
-                        else mu2 = (R)(l * l) / (R)m;
+                        if (sizeof(R) == 4) {
+                            const float mu = (float)l * rsm;
+                            mu2 = (R)(mu * mu);
+                        } else {
+                            mu2 = (R)(l * l) / (R)m;
+                        }
                         const R t2 = pw * mu2;
                         runm2 += t2;
                         runm4 += t2 * mu2;

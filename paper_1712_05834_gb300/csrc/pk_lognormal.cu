@@ -63,6 +63,27 @@ __device__ __forceinline__ Philox4x64 philox4x64(unsigned long long c0, unsigned
     return o;
 }
 
+// (row, col) of a flat index in rows of width w, advanced by a fixed stride
+// with one division at the start instead of one per step.
+struct Walk {
+    long long row, drow;
+    int col, dcol, w;
+    __device__ __forceinline__ Walk(long long f, long long stride, int width) : w(width) {
+        row = f / w;
+        col = (int)(f - row * w);
+        drow = stride / w;
+        dcol = (int)(stride - drow * w);
+    }
+    __device__ __forceinline__ void step() {
+        row += drow;
+        col += dcol;
+        if (col >= w) {
+            col -= w;
+            ++row;
+        }
+    }
+};
+
 // ((x >> 40) + 1/2) 2^-24: exact in FP32, strictly inside (0, 1).
 __device__ __forceinline__ float uniform24(unsigned long long x) {
     return ((float)(unsigned)(x >> 40) + 0.5f) * 5.9604644775390625e-8f;
@@ -71,8 +92,9 @@ __device__ __forceinline__ float uniform24(unsigned long long x) {
 __global__ void __launch_bounds__(kLnThreads)
 k_ln_noise(float *__restrict__ g, int ng, long long pitch, unsigned long long seed) {
     const long long ncell = (long long)ng * ng * ng;
-    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; 4 * b < ncell;
-         b += (long long)gridDim.x * blockDim.x) {
+    const long long b0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+    Walk w(4 * b0, 4 * stride, ng);                   // cell 4b
+    for (long long b = b0; 4 * b < ncell; b += stride, w.step()) {
         const Philox4x64 r = philox4x64((unsigned long long)b, seed, 0ull);
 #pragma unroll
         for (int pair = 0; pair < 2; ++pair) {
@@ -82,9 +104,12 @@ k_ln_noise(float *__restrict__ g, int ng, long long pitch, unsigned long long se
             sincospif(2.0f * u2, &sn, &cs);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const long long c = 4 * b + 2 * pair + h;
-                const long long row = c / ng;
-                const int l = (int)(c - row * ng);
+                int l = w.col + 2 * pair + h;              // the 4 cells may cross into the next row
+                long long row = w.row;
+                if (l >= ng) {
+                    l -= ng;
+                    ++row;
+                }
                 g[row * pitch + l] = h ? rad * sn : rad * cs;
             }
         }
@@ -96,11 +121,12 @@ k_ln_shape(float2 *__restrict__ gk, float2 *__restrict__ psik, int ng, float kf2
            float quarter_slope, float inv_n3, float kf) {
     const int nh = ng / 2 + 1;
     const long long nmodes = (long long)ng * ng * nh;
-    for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < nmodes;
-         f += (long long)gridDim.x * blockDim.x) {
-        const long long row = f / nh;
-        const int l = (int)(f - row * nh);
-        const int i = (int)(row / ng), j = (int)(row - (long long)i * ng);
+    const long long f0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+    Walk w(f0, stride, nh);
+    for (long long f = f0; f < nmodes; f += stride, w.step()) {
+        const int l = w.col;
+        const int irow = (int)w.row;                    // < ng^2 <= 2^22
+        const int i = irow / ng, j = irow - i * ng;
         const int ip = i < ng / 2 ? i : i - ng, jp = j < ng / 2 ? j : j - ng;
         const float m = (float)(ip * ip + jp * jp + l * l);
         float2 v = gk[f];
@@ -129,10 +155,10 @@ __global__ void __launch_bounds__(kLnThreads)
 k_ln_moments(const float *__restrict__ g, int ng, long long pitch, double *__restrict__ stats) {
     const long long ncell = (long long)ng * ng * ng;
     double s1 = 0.0, s2 = 0.0;
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
-         c += (long long)gridDim.x * blockDim.x) {
-        const long long row = c / ng;
-        const double v = (double)g[row * pitch + (c - row * ng)];
+    const long long c0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+    Walk w(c0, stride, ng);
+    for (long long c = c0; c < ncell; c += stride, w.step()) {
+        const double v = (double)g[w.row * pitch + w.col];
         s1 += v;
         s2 += v * v;
     }
@@ -164,10 +190,10 @@ k_ln_weights(const float *__restrict__ g, int ng, long long pitch, const double 
     const long long ncell = (long long)ng * ng * ng;
     const double mean = stats[0] / (double)ncell;
     const float half_var = (float)(0.5 * (stats[1] / (double)ncell - mean * mean));
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
-         c += (long long)gridDim.x * blockDim.x) {
-        const long long row = c / ng;
-        const float x = g[row * pitch + (c - row * ng)] - half_var;
+    const long long c0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+    Walk w(c0, stride, ng);
+    for (long long c = c0; c < ncell; c += stride, w.step()) {
+        const float x = g[w.row * pitch + w.col] - half_var;
         q[c] = (unsigned long long)__float2ll_rn(expf(x) * 1073741824.0f);
     }
 }
