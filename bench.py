@@ -142,13 +142,21 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """The largest x over all ranks (the slowest rank's time sets the job's)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds_max):
+    """Whole-job throughput of a weak-scaling run: every rank processes its own
+    units, the job ends with the slowest rank."""
+    return world * units_per_rank / seconds_max
 
 
 # --------------------------------------------------------------- oracle leg --
@@ -605,7 +613,7 @@ def main():
     if rank != 0:
         return 0
     K = args.steps
-    value = world * K / total_s
+    value = job_rate(world, K, total_s)
     med = {s: statistics.median(v) for s, v in stages.items()}
     nmodes = NMESH * NMESH * (NMESH // 2 + 1)
     nbinned = binned_stored_modes()

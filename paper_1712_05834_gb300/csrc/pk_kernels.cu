@@ -62,6 +62,7 @@ constexpr int kSegments = 75;         // (neighbour, class range) segments per t
 constexpr int kReduceChunk = 32;      // per-CTA histograms summed per reduce block
 constexpr int kStage = 256;           // candidates staged in shared memory per batch (small: 6 CTAs / SM)
 constexpr int kUploadChunk = 256;     // int64 values per parameter upload (2 KB)
+constexpr bool kTrashDeposit = true;
 
 __device__ __forceinline__ int wrapmod(int a, int n) {
     int r = a % n;
@@ -427,6 +428,51 @@ __device__ __forceinline__ void deposit(unsigned *lo, unsigned *hi, unsigned lon
     }
 }
 
+// MODE 2 deposit without branches: every one of the P^3 cells gets its
+// atomic on sm[idx].  Per axis, an offset outside the tile is a large negative
+// sentinel, so the index sum of a cell outside the tile is negative and
+// min((unsigned)sum, trash) sends it to the lane's scratch word sm[trash]
+// (never read); the lanes of a warp never split on tile bounds.  cell0: the
+// first word of the mesh's cells in sm.
+template <int P, int TC>
+__device__ __forceinline__ void deposit_flat(unsigned *sm, int cell0, unsigned trash, int T, float x, float y,
+                                             float z, float ws) {
+    int bx, by, bz;
+    float wx[P], wy[P], wz[P];
+    spline_weights<P>(x, bx, wx);
+    spline_weights<P>(y, by, wy);
+    spline_weights<P>(z, bz, wz);
+    const int TT = TC > 0 ? TC : T;
+    constexpr int kOut = -(1 << 24);
+    int ox[P], oy[P], oz[P];
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+        const int cx = bx + a, cy = by + a, cz = bz + a;
+        ox[a] = (unsigned)cx < (unsigned)TT ? cell0 + cx * TT * TT : kOut;
+        oy[a] = (unsigned)cy < (unsigned)TT ? cy * TT : kOut;
+        oz[a] = (unsigned)cz < (unsigned)TT ? cz : kOut;
+    }
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+        const float vxw = ws * wx[a];
+#pragma unroll
+        for (int b = 0; b < P; ++b) {
+            const float vxy = vxw * wy[b];
+            const int oab = ox[a] + oy[b];
+#pragma unroll
+            for (int c = 0; c < P; ++c) {
+                const unsigned q = __float_as_uint(fmaf(vxy, wz[c], 8388608.0f)) - 0x4B000000u;
+                if (kTrashDeposit) {
+                    atomicAdd(sm + min((unsigned)(oab + oz[c]), trash), q);
+                } else {
+                    const int idx = oab + oz[c];
+                    if (idx >= 0) atomicAdd(sm + idx, q);
+                }
+            }
+        }
+    }
+}
+
 // Correctly rounded int64 -> float without the 64-bit conversion instruction.
 __device__ __forceinline__ float ll_to_float_rn(long long q) {
     if (q == 0) return 0.0f;
@@ -682,32 +728,36 @@ k_paint_tiles(const float4 *__restrict__ sorted, const uint32_t *__restrict__ of
     }
     const float scale = ldexpf(1.0f, S);
     const float inv_scale = ldexpf(1.0f, -S);
-    // With no split needed (unit weights, sparse tile) both meshes of an
-    // interlaced pair are painted in one sweep: mesh 0 into lo, mesh 1 into hi,
-    // each candidate read once straight from the sorted copy (nothing to stage).
-    const bool both = NM == 2 && sp.fast == 2;
+    // With no split needed (unit weights, sparse tile) the tile is painted in
+    // one sweep over its candidates, each read once straight from the sorted
+    // copy (nothing to stage), with branch-free deposits; an interlaced pair
+    // goes into lo (mesh 0) and hi (mesh 1) together.
+    const bool sweep = sp.fast == 2;
     const bool staged_once = total <= (uint32_t)kStage;
-    if (staged_once && !both) stage_candidates(sorted, s_beg, s_pre, T, 0u, total, scale, cand);
+    if (staged_once && !sweep) stage_candidates(sorted, s_beg, s_pre, T, 0u, total, scale, cand);
     const long long pitch = 2LL * (g.N / 2 + 1);
     M *base = mesh + item * item_stride;
 
-    const int passes = both ? 1 : NM;
+    const int passes = sweep ? 1 : NM;
     const long long tile_off = ((long long)tx * T * g.N + (long long)ty * T) * pitch + (long long)tz * T;
 #pragma unroll 1
     for (int m = 0; m < passes; ++m) {
         {
             uint4 *z4 = reinterpret_cast<uint4 *>(smu);
-            const int n4 = (2 * T3) / 4;
+            const int nw = (sweep && NM == 1) ? T3 : 2 * T3;     // a single unsplit mesh uses lo only
+            const int n4 = nw / 4;
             for (int c = threadIdx.x; c < n4; c += blockDim.x) z4[c] = make_uint4(0u, 0u, 0u, 0u);
-            for (int c = 4 * n4 + threadIdx.x; c < 2 * T3; c += blockDim.x) smu[c] = 0u;
+            for (int c = 4 * n4 + threadIdx.x; c < nw; c += blockDim.x) smu[c] = 0u;
         }
         __syncthreads();
         const float sh = m ? 0.5f : 0.0f;
-        if (both) {
+        if (sweep) {
+            // the staging area is unused here: its first 32 words are the lanes' scratch
+            const unsigned trash = (unsigned)(2 * T3) + (threadIdx.x & 31);
             for (uint32_t k = threadIdx.x; k < total; k += blockDim.x) {
                 const float4 v = fetch_candidate(sorted, s_beg, s_pre, T, k, scale);
-                deposit<P, 2, TC>(lo, nullptr, nullptr, sp, T, v.x, v.y, v.z, v.w);
-                deposit<P, 2, TC>(hi, nullptr, nullptr, sp, T, v.x + 0.5f, v.y + 0.5f, v.z + 0.5f, v.w);
+                deposit_flat<P, TC>(smu, 0, trash, T, v.x, v.y, v.z, v.w);
+                if (NM == 2) deposit_flat<P, TC>(smu, T3, trash, T, v.x + 0.5f, v.y + 0.5f, v.z + 0.5f, v.w);
             }
         } else if (staged_once) {
             deposit_any<P, TC>(cand, total, lo, hi, acc64, sp, T, sh);
@@ -721,10 +771,11 @@ k_paint_tiles(const float4 *__restrict__ sorted, const uint32_t *__restrict__ of
             }
         }
         __syncthreads();
-        if (both) {
+        if (sweep) {
             flush_tile<M, TC>(lo, nullptr, nullptr, sp, inv_scale, base + tile_off, T, g.N, pitch, accumulate);
-            flush_tile<M, TC>(hi, nullptr, nullptr, sp, inv_scale, base + mesh_stride + tile_off, T, g.N, pitch,
-                              accumulate);
+            if (NM == 2)
+                flush_tile<M, TC>(hi, nullptr, nullptr, sp, inv_scale, base + mesh_stride + tile_off, T, g.N, pitch,
+                                  accumulate);
         } else {
             flush_tile<M, TC>(sp.fast ? lo : nullptr, sp.fast == 1 ? hi : nullptr, sp.fast ? nullptr : acc64, sp,
                               inv_scale, base + m * mesh_stride + tile_off, T, g.N, pitch, accumulate);
