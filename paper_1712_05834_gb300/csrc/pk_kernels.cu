@@ -62,7 +62,10 @@ constexpr int kSegments = 75;         // (neighbour, class range) segments per t
 constexpr int kReduceChunk = 32;      // per-CTA histograms summed per reduce block
 constexpr int kStage = 256;           // candidates staged in shared memory per batch (small: 6 CTAs / SM)
 constexpr int kUploadChunk = 256;     // int64 values per parameter upload (2 KB)
-constexpr bool kTrashDeposit = true;
+// Sweep paint: tiles with at most this many candidates use branch-free
+// deposits; denser tiles (e.g. uniform lattices, ~900 candidates per 16^3
+// tile) were measured faster with deposits that skip cells outside the tile.
+constexpr int kFlatMaxCand = 640;
 
 __device__ __forceinline__ int wrapmod(int a, int n) {
     int r = a % n;
@@ -462,12 +465,7 @@ __device__ __forceinline__ void deposit_flat(unsigned *sm, int cell0, unsigned t
 #pragma unroll
             for (int c = 0; c < P; ++c) {
                 const unsigned q = __float_as_uint(fmaf(vxy, wz[c], 8388608.0f)) - 0x4B000000u;
-                if (kTrashDeposit) {
-                    atomicAdd(sm + min((unsigned)(oab + oz[c]), trash), q);
-                } else {
-                    const int idx = oab + oz[c];
-                    if (idx >= 0) atomicAdd(sm + idx, q);
-                }
+                atomicAdd(sm + min((unsigned)(oab + oz[c]), trash), q);
             }
         }
     }
@@ -754,10 +752,16 @@ k_paint_tiles(const float4 *__restrict__ sorted, const uint32_t *__restrict__ of
         if (sweep) {
             // the staging area is unused here: its first 32 words are the lanes' scratch
             const unsigned trash = (unsigned)(2 * T3) + (threadIdx.x & 31);
+            const bool flat = total <= (uint32_t)kFlatMaxCand;
             for (uint32_t k = threadIdx.x; k < total; k += blockDim.x) {
                 const float4 v = fetch_candidate(sorted, s_beg, s_pre, T, k, scale);
-                deposit_flat<P, TC>(smu, 0, trash, T, v.x, v.y, v.z, v.w);
-                if (NM == 2) deposit_flat<P, TC>(smu, T3, trash, T, v.x + 0.5f, v.y + 0.5f, v.z + 0.5f, v.w);
+                if (flat) {
+                    deposit_flat<P, TC>(smu, 0, trash, T, v.x, v.y, v.z, v.w);
+                    if (NM == 2) deposit_flat<P, TC>(smu, T3, trash, T, v.x + 0.5f, v.y + 0.5f, v.z + 0.5f, v.w);
+                } else {
+                    deposit<P, 2, TC>(lo, nullptr, nullptr, sp, T, v.x, v.y, v.z, v.w);
+                    if (NM == 2) deposit<P, 2, TC>(hi, nullptr, nullptr, sp, T, v.x + 0.5f, v.y + 0.5f, v.z + 0.5f, v.w);
+                }
             }
         } else if (staged_once) {
             deposit_any<P, TC>(cand, total, lo, hi, acc64, sp, T, sh);
