@@ -157,3 +157,71 @@ def mock_set_specs(n_mocks: int, seed: int, n_lo: float = 2e5, n_hi: float = 4e6
     wi = rng.integers(0, len(windows), n_mocks)
     return [{"n": int(ns[i]), "nmesh": int(nm[i]), "window": windows[int(wi[i])],
              "seed": int(seed) + 1 + i} for i in range(n_mocks)]
+
+
+# ----------------------------------------------------------------------
+# Survey-like catalogs (the ConvolvedFFTPower workload, Sec. 3.4.1): an
+# observer at the origin, objects in a shell octant with a radial selection,
+# randoms drawn from the same selection.  Columns only: positions, the
+# selection's expected density `nbar`, completeness weights.
+# ----------------------------------------------------------------------
+
+def radial_selection(r, r_min: float, r_max: float):
+    """Selection probability of a survey shell: a smooth bump peaking at the
+    shell's middle, zero outside [r_min, r_max]."""
+    r = np.asarray(r, dtype=np.float64)
+    mid, half = 0.5 * (r_min + r_max), 0.5 * (r_max - r_min)
+    s = np.exp(-((r - mid) / (0.6 * half)) ** 2)
+    return np.where((r >= r_min) & (r <= r_max), s, 0.0)
+
+
+def _thin_to_shell(pos: np.ndarray, r_min: float, r_max: float, rng, n_keep: int):
+    """Keep objects with probability radial_selection(|x|), the first n_keep."""
+    r = np.sqrt(np.sum(pos * pos, axis=1))
+    keep = rng.random(len(pos)) < radial_selection(r, r_min, r_max)
+    out = pos[keep]
+    return out[:n_keep]
+
+
+def survey_catalogs(n_data: int, n_randoms: int, extent: float, seed: int, ngrid: int = 64,
+                    clustered: bool = True, device="cpu") -> dict:
+    """Data and randoms of a synthetic survey in observer-frame Cartesian
+    coordinates (Mpc/h): the octant x, y, z in [0, extent) with radii in
+    [0.2, 0.95] extent and the radial_selection bump.  Data: a log-normal
+    catalog (no RSD) of the cube, thinned by the selection (clustered=False:
+    uniform instead); randoms: uniform in the cube, thinned the same way.
+    Returns float64 numpy arrays: data / randoms (n, 3), their nbar (the
+    expected data density n0 sel(r) with n0 the cube's density before
+    thinning), data completeness weights in [0.8, 1.2], and the radii."""
+    rng = np.random.default_rng(seed)
+    r_min, r_max = 0.2 * extent, 0.95 * extent
+    probe = rng.random((200000, 3)) * extent
+    eff = float(np.mean(radial_selection(np.sqrt(np.sum(probe * probe, axis=1)), r_min, r_max)))
+    n_gen_d = int(math.ceil(1.15 * n_data / eff)) + 1000
+    n_gen_r = int(math.ceil(1.15 * n_randoms / eff)) + 1000
+    if clustered:
+        d = lognormal_catalog(n_gen_d, extent, ngrid, seed, f_rsd=0.0, device=device,
+                              dtype=torch.float64).cpu().numpy()
+    else:
+        d = rng.random((n_gen_d, 3)) * extent
+    data = _thin_to_shell(d, r_min, r_max, rng, n_data)
+    rand = _thin_to_shell(rng.random((n_gen_r, 3)) * extent, r_min, r_max, rng, n_randoms)
+    n0 = n_gen_d / extent ** 3
+    nbar = lambda p: n0 * radial_selection(np.sqrt(np.sum(p * p, axis=1)), r_min, r_max)
+    return {"data": data, "randoms": rand, "data_nbar": nbar(data), "rand_nbar": nbar(rand),
+            "data_wcomp": rng.uniform(0.8, 1.2, len(data)), "extent": extent,
+            "r_min": r_min, "r_max": r_max}
+
+
+def survey_sky(n: int, seed: int, ra=(10.0, 80.0), dec=(5.0, 55.0), z=(0.15, 0.7)) -> dict:
+    """Sky coordinates of n objects: RA uniform (degrees), uniform on the
+    sphere in Dec (sin Dec uniform), redshift with density growing as z^2
+    over the range; plus a stand-in n(z) column (a smooth positive function
+    of z, 1e-4 to 4e-4) and completeness weights in [0.8, 1.2]."""
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(ra[0], ra[1], n)
+    s0, s1 = math.sin(math.radians(dec[0])), math.sin(math.radians(dec[1]))
+    d = np.degrees(np.arcsin(rng.uniform(s0, s1, n)))
+    zz = (rng.uniform(z[0] ** 3, z[1] ** 3, n)) ** (1.0 / 3.0)
+    nz = 1e-4 * (2.5 + 1.5 * np.cos(2 * math.pi * (zz - z[0]) / (z[1] - z[0])))
+    return {"ra": r, "dec": d, "z": zz, "nbar": nz, "wcomp": rng.uniform(0.8, 1.2, n)}
