@@ -37,8 +37,10 @@ Readings where the paper is silent:
     A_0 only;
   * interlacing combines the two painted meshes in Fourier space,
     (F~_1 + F~_2 exp(i k.(H/2)(1,1,1))) / 2, and the multipole fields are
-    built from the inverse transform of that combination; the window
-    compensation divides the binned products by W^2(k);
+    built from the inverse transform of that combination, without the modes
+    that have an index at N/2 (their half-cell phase has no sign that keeps
+    the combination Hermitian, and they lie at |k| >= k_N, outside every
+    bin); the window compensation divides the binned products by W^2(k);
   * k bins, the mode weights h (1 on the l_z = 0 and N/2 planes, else 2) and
     the exclusion of k = 0 follow the periodic-box estimator of this oracle;
   * distances: flat LambdaCDM without radiation, chi(z) = (c / H0)
@@ -128,7 +130,8 @@ def fkp_meshes(data_pos, data_w, rand_pos, rand_w, alpha: float, box_size: float
 
 
 def interlaced_field(F1, F2):
-    """Real field whose transform is (F~_1 + F~_2 exp(i pi (n_x + n_y + n_z) / N)) / 2."""
+    """Real field whose transform is (F~_1 + F~_2 exp(i pi (n_x + n_y + n_z) / N)) / 2
+    on every mode with no index at N/2 (those set to zero)."""
     if F2 is None:
         return np.asarray(F1, dtype=np.float64)
     N = F1.shape[0]
@@ -136,6 +139,10 @@ def interlaced_field(F1, F2):
     fz = np.fft.rfftfreq(N, 1.0 / N)
     ph = np.exp(1j * math.pi * (f[:, None, None] + f[None, :, None] + fz[None, None, :]) / N)
     C = 0.5 * (np.fft.rfftn(F1) + np.fft.rfftn(F2) * ph)
+    h = N // 2
+    C[h, :, :] = 0.0
+    C[:, h, :] = 0.0
+    C[:, :, h] = 0.0
     return np.fft.irfftn(C, s=F1.shape, axes=(0, 1, 2))
 
 
