@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--no-study", action="store_true", help="skip the window / interlacing accuracy study")
+    ap.add_argument("--no-survey", action="store_true", help="skip the survey-multipole measurement")
     ap.add_argument("--profile", action="store_true",
                     help="timed steps only (no e2e leg, no CPU baseline, no clock sampler): for ncu")
     return ap.parse_args()
@@ -188,20 +189,21 @@ def oracle_sample_text():
             (ORACLE_PAINT_FRACTION, ORACLE_PAINT_FRACTION))
 
 
-def binned_stored_modes():
+def binned_stored_modes(N=None, box=None, dk=None):
     """Stored half-grid modes that fall in a k bin (0 < |k|, kmin <= k < kmax):
     the modes the bin pass must read.  Same FP64 bin rule as the library."""
     import numpy as np
-    N = NMESH
-    kF = (2.0 * math.pi) / L_BOX
-    nk = int(math.floor(((math.pi * N) / L_BOX) / DK))
+    N = N or NMESH
+    L_box, DK_ = box or L_BOX, dk or DK
+    kF = (2.0 * math.pi) / L_box
+    nk = int(math.floor(((math.pi * N) / L_box) / DK_))
     f = np.where(np.arange(N) < N // 2, np.arange(N), np.arange(N) - N)
     r2 = (f[:, None] ** 2 + f[None, :] ** 2).reshape(-1)
     l2 = np.arange(N // 2 + 1) ** 2
     total = 0
-    for chunk in np.array_split(r2, 64):
+    for chunk in np.array_split(r2, max(64, N * N // 8192)):
         m = chunk[:, None] + l2[None, :]
-        b = np.floor((kF * np.sqrt(m.astype(np.float64)) - 0.0) / DK)
+        b = np.floor((kF * np.sqrt(m.astype(np.float64)) - 0.0) / DK_)
         total += int(np.count_nonzero((m > 0) & (b >= 0) & (b < nk)))
     return total
 
@@ -526,6 +528,80 @@ def measure_window_study(torch, rank):
             "wall_s": wall}
 
 
+def measure_survey(pk, torch, stream, world, rank, steps=5, warmup=2):
+    """Survey multipoles (ConvolvedFFTPower) on the paper's "small" benchmark
+    sample: 1e6 galaxies in a 2500 Mpc/h survey volume, Nmesh 1024, l = 0, 2,
+    4 (1 + 5 + 9 = 15 r2c FFTs), here with 1e7 randoms, CIC, compensated."""
+    import numpy as np
+    import synth
+    ext, N, dk = 2500.0, 1024, 0.005
+    t0 = time.perf_counter()
+    c = synth.survey_catalogs(1_000_000, 10_000_000, ext, synth.seed_for(9, 100 + rank), ngrid=256,
+                              device="cuda")
+    gen_s = time.perf_counter() - t0
+    L, origin = 1.04 * ext, (-0.02 * ext,) * 3
+    nd, nr = len(c["data"]), len(c["randoms"])
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    dp, dw, dn, rp, rn = (dev(c["data"]), dev(c["data_wcomp"]), dev(c["data_nbar"]), dev(c["randoms"]),
+                          dev(c["rand_nbar"]))
+    del c
+    gd = pk.survey_catalog(dp, wcomp=dw, nbar=dn)
+    gr = pk.survey_catalog(rp, nbar=rn)
+    cfg = pk.make_survey_config(L, origin, N, "cic", False, dk=dk, capacity=nd + nr)
+    plan = pk.pk_survey_plan(cfg, stream)
+    pk.pk_survey_enable_timing(plan, True)
+    times, stages = [], {s: [] for s in pk.SURVEY_STAGES}
+    try:
+        for k in range(warmup + steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pk.pk_survey_paint(plan, gd, gr)
+            pk.pk_survey_compute(plan)
+            res = pk.pk_survey_result(plan)
+            b.record(stream)
+            b.synchronize()
+            st = pk.pk_survey_stage_times(plan)
+            if k >= warmup:
+                times.append(a.elapsed_time(b))
+                for s_ in pk.SURVEY_STAGES:
+                    stages[s_].append(st[s_])
+        launches = pk.pk_survey_launch_count(plan)
+        free, total = torch.cuda.mem_get_info()
+    finally:
+        pk.pk_survey_destroy(plan)
+        del dp, dw, dn, rp, rn
+        torch.cuda.empty_cache()
+    total_s = max_over_ranks(sum(times) / 1e3, world)
+    med = {s_: statistics.median(v) for s_, v in stages.items()}
+    hbm, peak_kind = peaks()
+    nbinned = binned_stored_modes(N, L, dk)
+    cells = N ** 3
+    bin_bytes = 15 * nbinned * 8                   # A_0 + 14 Y_lm transforms, complex64 per binned mode
+    field_bytes = cells * (2 * 4 + 15 * 4)         # read D, R; write F (A_0) + 14 weighted copies
+    roof = {
+        "k_survey_bin": {"ms": med["bin"], "bytes": bin_bytes,
+                         "per_unit": "8 B per binned stored mode per transform (15 transforms)"},
+        "k_survey_ylm": {"ms": med["field"], "bytes": field_bytes,
+                         "per_unit": "8 B read + 60 B written per cell (D, R in; F and 14 F Y_lm out)"},
+    }
+    for r in roof.values():
+        r["achieved"] = r["bytes"] / r["ms"] / 1e6
+        r["bound"], r["peak"], r["frac"], r["unit"] = "hbm", hbm, r["bytes"] / r["ms"] / 1e6 / hbm, "GB/s"
+        r["peak_kind"] = peak_kind
+    ok = res["modes"] > 0
+    kk = res["k"][ok]
+    pick = np.unique(np.searchsorted(kk, [0.02, 0.05, 0.1, 0.2, 0.5]).clip(0, len(kk) - 1))
+    return {"workload": "survey octant (observer at the corner, radii 0.2-0.95 x 2500 Mpc/h, radial "
+                        "selection), 1e6 clustered galaxies (log-normal) + 1e7 randoms, box 2600 Mpc/h, "
+                        "Nmesh 1024, CIC, compensated, dk 0.005 to k_N, l = 0, 2, 4 (15 r2c FFTs), FKP sums FP64",
+            "multipoles_per_s": world * steps / total_s, "ms_per_step": 1e3 * total_s / steps,
+            "stage_ms_median": med, "fft_count_per_step": 15,
+            "objects_per_step": nd + nr, "rooflines": roof, "gpu_launches_per_step": launches // (warmup + steps),
+            "alpha": res["alpha"], "shot_noise": res["shot_noise"],
+            "poles_at": {"%.3f" % kk[i]: [float(res["poles"][r_][ok][i]) for r_ in range(3)] for i in pick},
+            "device_mem_used_gb": (total - free) / 1e9, "generation_s": gen_s}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -609,6 +685,7 @@ def main():
         served = None if (args.no_serve or args.profile) else measure_serving(pk, torch, world, rank,
                                                                               args.serve_requests)
         study = None if (args.no_study or args.profile) else measure_window_study(torch, rank)
+        survey = None if (args.no_survey or args.profile) else measure_survey(pk, torch, stream, world, rank)
 
     if rank != 0:
         return 0
@@ -672,6 +749,8 @@ def main():
         line["serving"] = served
     if study is not None:
         line["window_study"] = study
+    if survey is not None:
+        line["survey_multipoles"] = survey
     if world == 1 and not args.no_cpu_baseline and not args.profile:
         import oracle
         oracle.build()

@@ -372,6 +372,168 @@ const char *pk_lognormal_error(pk_lognormal_t gen);
 /* Free the generator (waits for its stream).  NULL is a no-op. */
 pk_status pk_lognormal_destroy(pk_lognormal_t gen);
 
+/* ---- Survey multipoles (ConvolvedFFTPower, Sec. 3.4.1) ----
+ * Power-spectrum multipoles of survey data (positions as right ascension,
+ * declination and redshift, or observer-frame Cartesian), with the line of
+ * sight from the observer to each point.  The paper names the estimator by
+ * reference (the FFT-based estimator of Hand et al. 2017, 2l + 1 FFTs for
+ * multipole l, after Bianchi et al. 2015, Scoccimarro 2015, Feldman, Kaiser &
+ * Peacock 1994 and Yamamoto et al. 2006).  What the library computes:
+ *   w      = w_comp w_fkp per object; w_fkp = 1 / (1 + nbar P0) when the
+ *            config's p0_fkp > 0, else the given column (NULL = 1);
+ *   alpha  = sum_data w_comp / sum_randoms w_comp;
+ *   F      = painted data - alpha painted randoms, on the mesh whose node c
+ *            sits at box_origin + c H (observer frame, observer at 0); with
+ *            interlacing the two meshes are combined in Fourier space as in
+ *            pk_compute and transformed back to one real field;
+ *   A_0    = FFT[F];  A_l(k) = (4 pi / (2l + 1)) sum_m Y_lm(k^) FFT[F Y_lm(x^)](k)
+ *            with the real spherical harmonics Y_lm (pk_survey_ylm) and x^
+ *            the unit vector of node c (a node at the observer contributes to
+ *            A_0 only); by the addition theorem A_l is the sum over nodes of
+ *            F exp(-i k.x) L_l(k^.x^) (the phase of box_origin dropped);
+ *   P_l(k) = (2l + 1) / I < Re[A_l A_0^*] / W^2(k) >_bin - [l = 0] S, with the
+ *            k bins, mode weights and window W(k) of pk_compute,
+ *            I = alpha sum_randoms nbar w_comp w_fkp^2 and
+ *            S = (sum_data w^2 + alpha^2 sum_randoms w^2) / I.
+ * Distances for sky input: flat LambdaCDM without radiation,
+ * chi(z) = (c / H0) int_0^z dz' / sqrt(Om (1 + z')^3 + 1 - Om) in Mpc/h with
+ * c / H0 = 2997.92458 Mpc/h; x = chi (cos Dec cos RA, cos Dec sin RA, sin Dec),
+ * RA and Dec in degrees.  The library tabulates chi and its derivative at
+ * 8192 redshifts in [0, zmax] (FP64 on the host) and interpolates with cubic
+ * Hermite polynomials in FP64 on the device. */
+typedef struct pk_survey_s *pk_survey_t;
+
+typedef enum {
+    PK_COORD_CARTESIAN = 0,   /* x, y, z in Mpc/h, observer at the origin         */
+    PK_COORD_SKY = 1          /* RA (deg), Dec (deg), redshift z                  */
+} pk_coord;
+
+typedef struct {
+    double box_size;        /* L > 0: edge of the cubic mesh box (Mpc/h)         */
+    double box_origin[3];   /* observer-frame position of mesh node (0, 0, 0)    */
+    int nmesh;              /* N: even, 4 <= N <= 4096                           */
+    int window;             /* pk_window                                         */
+    int interlaced;         /* 0 / 1                                             */
+    int compensated;        /* 0 / 1                                             */
+    double kmin, kmax, dk;  /* k bins as in pk_config (kmax <= 0 selects k_N)    */
+    unsigned poles_mask;    /* bit0 l=0, bit1 l=2, bit2 l=4 (l = 0 always runs)  */
+    int precision;          /* pk_precision                                      */
+    int subtract_shot;      /* 0 / 1: subtract S from P_0                        */
+    double omega_m;         /* matter density for PK_COORD_SKY, in (0, 1]; 0 when
+                               only Cartesian input is used                      */
+    double zmax;            /* largest redshift of the distance table (sky input);
+                               0 selects 5                                      */
+    double p0_fkp;          /* > 0: w_fkp = 1 / (1 + nbar P0); 0: given w_fkp    */
+    int max_batch;          /* Y_lm-weighted meshes per cuFFT call; 0: as many as
+                               fit in half the free device memory                */
+    int64_t capacity;       /* data + randoms objects to reserve (0: on demand)  */
+} pk_survey_config;
+
+/* One catalog for pk_survey_paint.  pos: n x 3 in the layout of `dtype`
+ * (PK_F32 or PK_F64): (x, y, z) for PK_COORD_CARTESIAN, (RA, Dec, z) for
+ * PK_COORD_SKY.  Columns are float arrays of n (device or host memory, like
+ * pos); NULL columns are 1.  nbar (the mean number density at the object) is
+ * required for the randoms and, when p0_fkp > 0, for the data. */
+typedef struct {
+    const void *pos;
+    int dtype;              /* pk_dtype: PK_F32 or PK_F64                        */
+    int coord;              /* pk_coord                                          */
+    const float *wcomp;     /* completeness weights                              */
+    const float *wfkp;      /* FKP weights (ignored when p0_fkp > 0)             */
+    const float *nbar;      /* n(z) at each object                               */
+    int64_t n;              /* >= 0                                              */
+} pk_survey_catalog;
+
+/* Fill *cfg with defaults: L = 1000, origin (0, 0, 0), N = 256, CIC, not
+ * interlaced, compensated, kmin = 0, kmax = k_N, dk = 2 kF, l = 0, 2, 4, FP32
+ * mesh, shot noise subtracted, Om = 0.31, zmax = 5, given FKP weights,
+ * automatic batch, no reserved capacity. */
+void pk_survey_config_default(pk_survey_config *cfg);
+
+/* Create a survey plan: validates cfg, allocates two catalogs' meshes, the
+ * A_0 transform, the Y_lm-weighted meshes of one cuFFT batch and the cuFFT
+ * plans, tabulates chi(z) when omega_m > 0, and computes the mode counts and
+ * mean k of the k bins.  All work runs on `cuda_stream`.  Errors: PK_EINVAL
+ * (message through pk_plan_error), PK_ENOMEM, PK_ECUDA, PK_ECUFFT; on error
+ * *out is NULL. */
+pk_status pk_survey_plan(const pk_survey_config *cfg, void *cuda_stream, pk_survey_t *out);
+
+/* Convert (sky input) and paint the data and randoms: each object becomes
+ * box-frame (x - box_origin, w) in FP32, the catalog sums of alpha, I and S
+ * are taken in FP64, and both catalogs are painted into their own meshes
+ * (int64 fixed point, as pk_paint).  randoms == NULL keeps the randoms
+ * painted by the previous call (mocks that share one random catalog).
+ * Objects outside the box wrap periodically and are counted in n_outside;
+ * sky objects with z outside [0, zmax] (or NaN) get weight 0 and are counted
+ * in n_rejected.  Asynchronous on the plan's stream; host arrays are copied
+ * first.  Errors: PK_EINVAL (dtype, coord, missing nbar, sky input without
+ * omega_m, NULL pos with n > 0), PK_ESTATE (randoms == NULL before any
+ * randoms), PK_ENOMEM, PK_ECUDA. */
+pk_status pk_survey_paint(pk_survey_t plan, const pk_survey_catalog *data, const pk_survey_catalog *randoms);
+
+/* Run the estimator on the painted catalogs: the FKP combination, the
+ * interlacing round trip (interlaced plans), 1 + 5 [l=2] + 9 [l=4] r2c
+ * transforms, the binning of A_0 and of every Y_lm-weighted transform, and
+ * the normalization.  Asynchronous; pk_survey_result waits.  Errors:
+ * PK_ESTATE (nothing painted), PK_ECUDA, PK_ECUFFT. */
+pk_status pk_survey_compute(pk_survey_t plan);
+
+typedef struct {
+    int nk, npoles;               /* npoles = 3: rows l = 0, 2, 4                 */
+    const double *k_edges;        /* nk + 1                                       */
+    const double *k_mean;         /* nk                                           */
+    const double *poles;          /* 3 * nk: P_0, P_2, P_4 (rows not asked: NaN;
+                                     empty bins: NaN)                              */
+    const uint64_t *modes;        /* nk                                           */
+    double alpha, norm, shot_noise;
+    double data_wsum, randoms_wsum;        /* sum w_comp                          */
+    double data_w2sum, randoms_w2sum;      /* sum (w_comp w_fkp)^2                */
+    double randoms_nsum;                   /* sum nbar w_comp w_fkp^2             */
+    int64_t n_data, n_randoms;
+    int64_t n_outside;            /* objects outside the box (wrapped)            */
+    int64_t n_rejected;           /* sky objects with z outside [0, zmax]         */
+} pk_survey_result_view;
+
+/* Wait for the last pk_survey_compute and describe its result; the pointers
+ * stay valid until the next compute or destroy.  Errors: PK_ESTATE (no
+ * compute), PK_ECUDA. */
+pk_status pk_survey_result(pk_survey_t plan, pk_survey_result_view *out);
+
+/* Real spherical harmonic Y_lm of the unit vector (x, y, z), l = 2 or 4,
+ * |m| <= l, orthonormal on the sphere (the functions the survey path
+ * evaluates on the device, here in FP64 on the host); NaN for other (l, m). */
+double pk_survey_ylm(int l, int m, double x, double y, double z);
+
+/* Stages whose device time pk_survey_stage_times reports. */
+typedef enum {
+    PK_SURVEY_STAGE_PREP = 0,    /* catalog conversion + sums (pk_survey_paint)     */
+    PK_SURVEY_STAGE_PAINT = 1,   /* tile sort + paint of both catalogs              */
+    PK_SURVEY_STAGE_FFT = 2,     /* every cuFFT call of pk_survey_compute           */
+    PK_SURVEY_STAGE_FIELD = 3,   /* FKP combine, interlacing, Y_lm weighting         */
+    PK_SURVEY_STAGE_BIN = 4,     /* per-mode sums of A_0 and the Y_lm transforms     */
+    PK_SURVEY_STAGE_FINAL = 5,   /* row reduce + normalization                      */
+    PK_SURVEY_NSTAGES = 6
+} pk_survey_stage;
+
+/* Turn per-stage timing on (1) or off (0): CUDA events around each stage of
+ * pk_survey_paint and pk_survey_compute on the plan's stream.  No effect on
+ * results. */
+pk_status pk_survey_enable_timing(pk_survey_t plan, int on);
+
+/* Device milliseconds per stage (PK_SURVEY_NSTAGES doubles) of the last
+ * timed paint and compute; waits for their events.  Errors: PK_ESTATE
+ * (timing off), PK_ECUDA. */
+pk_status pk_survey_stage_times(pk_survey_t plan, double *ms);
+
+/* Number of the library's own kernels launched on this survey plan. */
+long long pk_survey_launch_count(pk_survey_t plan);
+
+/* Message of the last failed call on this survey plan ("" if none). */
+const char *pk_survey_error(pk_survey_t plan);
+
+/* Free the survey plan (waits for its stream).  NULL is a no-op. */
+pk_status pk_survey_destroy(pk_survey_t plan);
+
 /* Free everything the plan owns (waits for its stream).  NULL is a no-op. */
 pk_status pk_destroy(pk_plan_t plan);
 

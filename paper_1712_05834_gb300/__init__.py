@@ -29,7 +29,8 @@ __all__ = [
     "PkError", "pk_config", "pk_config_default", "make_config", "pk_plan", "pk_paint",
     "pk_paint_many", "pk_compute", "pk_result", "pk_mesh", "pk_destroy", "pk_status_string",
     "pk_last_error", "pk_enable_timing", "pk_stage_times", "pk_launch_count", "FFTPower", "load",
-    "build",
+    "build", "make_survey_config", "survey_catalog", "pk_survey_plan", "pk_survey_paint", "pk_survey_compute",
+    "pk_survey_result", "pk_survey_ylm", "pk_survey_destroy", "ConvolvedFFTPower",
 ]
 
 PK_OK, PK_EINVAL, PK_ENOMEM, PK_ECUDA, PK_ECUFFT, PK_EOVERFLOW, PK_ETIMEOUT, PK_ESTATE = range(8)
@@ -43,7 +44,10 @@ EXPORTED = ["pk_config_default", "pk_plan", "pk_paint", "pk_paint_many", "pk_com
             "pk_result", "pk_mesh", "pk_destroy", "pk_status_string", "pk_last_error",
             "pk_plan_error", "pk_enable_timing", "pk_stage_times", "pk_launch_count",
             "pk_bin_static", "pk_cross", "pk_cross_result", "pk_paint_values", "pk_projected", "pk_lognormal_plan", "pk_lognormal_field", "pk_lognormal_draw",
-            "pk_lognormal_amp", "pk_lognormal_launch_count", "pk_lognormal_error", "pk_lognormal_destroy"]
+            "pk_lognormal_amp", "pk_lognormal_launch_count", "pk_lognormal_error", "pk_lognormal_destroy",
+            "pk_survey_config_default", "pk_survey_plan", "pk_survey_paint", "pk_survey_compute",
+            "pk_survey_result", "pk_survey_ylm", "pk_survey_launch_count", "pk_survey_error",
+            "pk_survey_destroy", "pk_survey_enable_timing", "pk_survey_stage_times"]
 STAGES = ["sort", "paint", "fft", "bin", "final"]
 
 
@@ -55,6 +59,25 @@ class pk_config(ctypes.Structure):
         ("poles_mask", ctypes.c_uint), ("los_axis", ctypes.c_int), ("precision", ctypes.c_int),
         ("subtract_shot", ctypes.c_int), ("fixed_scale_log2", ctypes.c_int), ("batch", ctypes.c_int),
         ("tile", ctypes.c_int), ("paint_variant", ctypes.c_int), ("capacity", ctypes.c_int64),
+    ]
+
+
+class pk_survey_config(ctypes.Structure):
+    _fields_ = [
+        ("box_size", ctypes.c_double), ("box_origin", ctypes.c_double * 3), ("nmesh", ctypes.c_int),
+        ("window", ctypes.c_int), ("interlaced", ctypes.c_int), ("compensated", ctypes.c_int),
+        ("kmin", ctypes.c_double), ("kmax", ctypes.c_double), ("dk", ctypes.c_double),
+        ("poles_mask", ctypes.c_uint), ("precision", ctypes.c_int), ("subtract_shot", ctypes.c_int),
+        ("omega_m", ctypes.c_double), ("zmax", ctypes.c_double), ("p0_fkp", ctypes.c_double),
+        ("max_batch", ctypes.c_int), ("capacity", ctypes.c_int64),
+    ]
+
+
+class pk_survey_catalog(ctypes.Structure):
+    _fields_ = [
+        ("pos", ctypes.c_void_p), ("dtype", ctypes.c_int), ("coord", ctypes.c_int),
+        ("wcomp", ctypes.c_void_p), ("wfkp", ctypes.c_void_p), ("nbar", ctypes.c_void_p),
+        ("n", ctypes.c_int64),
     ]
 
 
@@ -82,6 +105,16 @@ class pk_projected_view(ctypes.Structure):
     _fields_ = [
         ("nk", ctypes.c_int), ("ndim", ctypes.c_int), ("k_edges", _dp), ("k_mean", _dp), ("pk", _dp),
         ("modes", _up), ("shot_noise", ctypes.c_double), ("wsum", ctypes.c_double),
+    ]
+
+
+class pk_survey_result_view(ctypes.Structure):
+    _fields_ = [
+        ("nk", ctypes.c_int), ("npoles", ctypes.c_int), ("k_edges", _dp), ("k_mean", _dp), ("poles", _dp),
+        ("modes", _up), ("alpha", ctypes.c_double), ("norm", ctypes.c_double), ("shot_noise", ctypes.c_double),
+        ("data_wsum", ctypes.c_double), ("randoms_wsum", ctypes.c_double), ("data_w2sum", ctypes.c_double),
+        ("randoms_w2sum", ctypes.c_double), ("randoms_nsum", ctypes.c_double), ("n_data", ctypes.c_int64),
+        ("n_randoms", ctypes.c_int64), ("n_outside", ctypes.c_int64), ("n_rejected", ctypes.c_int64),
     ]
 
 
@@ -154,6 +187,28 @@ def load():
         lib.pk_lognormal_error.restype = ctypes.c_char_p
         lib.pk_lognormal_destroy.argtypes = [vp]
         lib.pk_lognormal_destroy.restype = i
+        lib.pk_survey_config_default.argtypes = [ctypes.POINTER(pk_survey_config)]
+        lib.pk_survey_config_default.restype = None
+        lib.pk_survey_plan.argtypes = [ctypes.POINTER(pk_survey_config), vp, ctypes.POINTER(vp)]
+        lib.pk_survey_plan.restype = i
+        lib.pk_survey_paint.argtypes = [vp, ctypes.POINTER(pk_survey_catalog), ctypes.POINTER(pk_survey_catalog)]
+        lib.pk_survey_paint.restype = i
+        lib.pk_survey_compute.argtypes = [vp]
+        lib.pk_survey_compute.restype = i
+        lib.pk_survey_result.argtypes = [vp, ctypes.POINTER(pk_survey_result_view)]
+        lib.pk_survey_result.restype = i
+        lib.pk_survey_ylm.argtypes = [i, i, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        lib.pk_survey_ylm.restype = ctypes.c_double
+        lib.pk_survey_launch_count.argtypes = [vp]
+        lib.pk_survey_launch_count.restype = ctypes.c_longlong
+        lib.pk_survey_error.argtypes = [vp]
+        lib.pk_survey_error.restype = ctypes.c_char_p
+        lib.pk_survey_enable_timing.argtypes = [vp, i]
+        lib.pk_survey_enable_timing.restype = i
+        lib.pk_survey_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+        lib.pk_survey_stage_times.restype = i
+        lib.pk_survey_destroy.argtypes = [vp]
+        lib.pk_survey_destroy.restype = i
         _lib = lib
     return _lib
 
@@ -483,6 +538,154 @@ class LogNormalCatalog:
         if self.gen:
             pk_lognormal_destroy(self.gen)
             self.gen = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- survey multipoles (pk_survey_*: the ConvolvedFFTPower of Sec. 3.4.1) ----
+
+PK_COORD_CARTESIAN, PK_COORD_SKY = 0, 1
+
+
+def _check_sv(status, plan):
+    if status != PK_OK:
+        raise PkError(status, load().pk_survey_error(plan).decode())
+
+
+def make_survey_config(box_size, box_origin, nmesh, window="cic", interlaced=False, compensated=True, dk=None,
+                       kmin=0.0, kmax=None, poles=(0, 2, 4), precision="f32", subtract_shot=True, omega_m=0.31,
+                       zmax=5.0, p0_fkp=0.0, max_batch=0, capacity=0) -> pk_survey_config:
+    """pk_survey_config from keywords (the ConvolvedFFTPower options: mesh,
+    window, interlacing, k bins, poles, FKP P0; omega_m for sky input)."""
+    c = pk_survey_config()
+    load().pk_survey_config_default(ctypes.byref(c))
+    c.box_size = float(box_size)
+    for a in range(3):
+        c.box_origin[a] = float(box_origin[a])
+    c.nmesh = int(nmesh)
+    c.window = WINDOWS[window] if isinstance(window, str) else int(window)
+    c.interlaced = int(bool(interlaced))
+    c.compensated = int(bool(compensated))
+    c.dk = float(dk) if dk is not None else 2.0 * (2.0 * math.pi) / float(box_size)
+    c.kmin = float(kmin)
+    c.kmax = 0.0 if kmax is None else float(kmax)
+    c.poles_mask = sum({0: 1, 2: 2, 4: 4}[ell] for ell in poles) | 1
+    c.precision = {"f32": PK_MESH_F32, "f64": PK_MESH_F64}[precision] if isinstance(precision, str) else int(precision)
+    c.subtract_shot = int(bool(subtract_shot))
+    c.omega_m = float(omega_m)
+    c.zmax = float(zmax)
+    c.p0_fkp = float(p0_fkp)
+    c.max_batch = int(max_batch)
+    c.capacity = int(capacity)
+    return c
+
+
+def pk_survey_plan(cfg: pk_survey_config, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().pk_survey_plan(ctypes.byref(cfg), _stream_ptr(stream), ctypes.byref(h)))
+    return h
+
+
+def _ptr_f32(a, n, name):
+    if a is None:
+        return None
+    if tuple(a.shape) != (n,):
+        raise ValueError("%s must have shape (n,)" % name)
+    if hasattr(a, "data_ptr"):
+        if str(a.dtype) != "torch.float32" or not a.is_contiguous():
+            raise ValueError("%s must be contiguous float32" % name)
+        return a.data_ptr()
+    if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("%s must be contiguous float32" % name)
+    return a.ctypes.data
+
+
+def survey_catalog(pos, coord="cartesian", wcomp=None, wfkp=None, nbar=None) -> pk_survey_catalog:
+    """pk_survey_catalog of an (n, 3) float32/float64 array (torch or numpy,
+    device or host): x, y, z (coord "cartesian") or RA, Dec, z ("sky")."""
+    ptr, code, n = _array_info(pos)
+    if code == PK_F32X4:
+        raise ValueError("survey positions must have shape (n, 3)")
+    return pk_survey_catalog(ptr, code, {"cartesian": PK_COORD_CARTESIAN, "sky": PK_COORD_SKY}[coord],
+                             _ptr_f32(wcomp, n, "wcomp"), _ptr_f32(wfkp, n, "wfkp"), _ptr_f32(nbar, n, "nbar"), n)
+
+
+def pk_survey_paint(plan, data: pk_survey_catalog, randoms: pk_survey_catalog | None = None):
+    """Paint the data and (unless None: keep the last ones) the randoms."""
+    _check_sv(load().pk_survey_paint(plan, ctypes.byref(data), None if randoms is None else ctypes.byref(randoms)),
+              plan)
+
+
+def pk_survey_compute(plan):
+    _check_sv(load().pk_survey_compute(plan), plan)
+
+
+def pk_survey_result(plan) -> dict:
+    v = pk_survey_result_view()
+    _check_sv(load().pk_survey_result(plan, ctypes.byref(v)), plan)
+    nk = v.nk
+    return {"nk": nk, "k_edges": _arr(v.k_edges, nk + 1), "k": _arr(v.k_mean, nk),
+            "poles": _arr(v.poles, 3 * nk).reshape(3, nk), "modes": _arr(v.modes, nk, np.int64),
+            "alpha": v.alpha, "norm": v.norm, "shot_noise": v.shot_noise, "data_wsum": v.data_wsum,
+            "randoms_wsum": v.randoms_wsum, "data_w2sum": v.data_w2sum, "randoms_w2sum": v.randoms_w2sum,
+            "randoms_nsum": v.randoms_nsum, "n_data": v.n_data, "n_randoms": v.n_randoms,
+            "n_outside": v.n_outside, "n_rejected": v.n_rejected}
+
+
+def pk_survey_ylm(l, m, x, y, z) -> float:
+    return float(load().pk_survey_ylm(int(l), int(m), float(x), float(y), float(z)))
+
+
+SURVEY_STAGES = ["prep", "paint", "fft", "field", "bin", "final"]
+
+
+def pk_survey_enable_timing(plan, on=True):
+    _check_sv(load().pk_survey_enable_timing(plan, int(bool(on))), plan)
+
+
+def pk_survey_stage_times(plan) -> dict:
+    """Device ms per stage of the last timed pk_survey_paint / pk_survey_compute."""
+    ms = (ctypes.c_double * len(SURVEY_STAGES))()
+    _check_sv(load().pk_survey_stage_times(plan, ms), plan)
+    return dict(zip(SURVEY_STAGES, list(ms)))
+
+
+def pk_survey_launch_count(plan) -> int:
+    return int(load().pk_survey_launch_count(plan))
+
+
+def pk_survey_destroy(plan):
+    if plan:
+        _check(load().pk_survey_destroy(plan))
+
+
+class ConvolvedFFTPower:
+    """Survey multipoles: ``ConvolvedFFTPower(cfg).run(data, randoms)`` with
+    catalogs made by ``survey_catalog``; randoms=None reuses the last ones."""
+
+    def __init__(self, cfg: pk_survey_config, stream=None):
+        self.cfg = cfg
+        self.plan = pk_survey_plan(cfg, stream)
+
+    def run(self, data, randoms=None):
+        pk_survey_paint(self.plan, data, randoms)
+        pk_survey_compute(self.plan)
+        return pk_survey_result(self.plan)
+
+    def close(self):
+        if self.plan:
+            pk_survey_destroy(self.plan)
+            self.plan = None
 
     def __enter__(self):
         return self

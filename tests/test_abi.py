@@ -97,7 +97,8 @@ def _c_layout(tmp_path, struct, fields):
     return int(out[0]), [int(v) for v in out[1:]]
 
 
-@pytest.mark.parametrize("name", ["pk_config", "pk_result_view", "pk_lognormal_config", "pk_projected_view"])
+@pytest.mark.parametrize("name", ["pk_config", "pk_result_view", "pk_lognormal_config", "pk_projected_view",
+                                  "pk_survey_config", "pk_survey_catalog", "pk_survey_result_view"])
 def test_ctypes_structs_match_the_header(pk, tmp_path, name):
     cls = getattr(pk, name)
     fields = [f for f, _ in cls._fields_]
@@ -130,3 +131,34 @@ def test_lognormal_null_arguments(pk):
     assert lib.pk_lognormal_draw(None, 1, 10, None) == pk.PK_EINVAL
     assert lib.pk_lognormal_field(None, 1, None) == pk.PK_EINVAL
     assert lib.pk_lognormal_destroy(None) == pk.PK_OK
+
+
+@pytest.mark.parametrize("field,value,word", [
+    ("box_size", -1.0, "box_size"), ("nmesh", 7, "nmesh"), ("window", 5, "window"), ("dk", 0.0, "dk"),
+    ("poles_mask", 8, "poles_mask"), ("omega_m", 1.5, "omega_m"), ("zmax", -1.0, "zmax"),
+    ("p0_fkp", -3.0, "p0_fkp"), ("max_batch", -1, "max_batch"), ("precision", 7, "precision"),
+])
+def test_survey_plan_rejects_bad_config(pk, field, value, word):
+    c = pk.make_survey_config(1000.0, (0.0, 0.0, 0.0), 32)
+    setattr(c, field, value)
+    h = ctypes.c_void_p()
+    assert pk.load().pk_survey_plan(ctypes.byref(c), None, ctypes.byref(h)) == pk.PK_EINVAL
+    assert not h.value
+    assert word in pk.load().pk_plan_error().decode()
+
+
+def test_survey_config_default(pk):
+    c = pk.pk_survey_config()
+    pk.load().pk_survey_config_default(ctypes.byref(c))
+    assert c.box_size == 1000.0 and c.nmesh == 256 and c.poles_mask == 7 and c.omega_m == 0.31
+    assert list(c.box_origin) == [0.0, 0.0, 0.0] and c.zmax == 5.0 and c.max_batch == 0
+
+
+def test_survey_null_arguments(pk):
+    lib = pk.load()
+    assert lib.pk_survey_plan(None, None, None) == pk.PK_EINVAL
+    assert lib.pk_survey_paint(None, None, None) == pk.PK_EINVAL
+    assert lib.pk_survey_compute(None) == pk.PK_EINVAL
+    assert lib.pk_survey_result(None, None) == pk.PK_EINVAL
+    assert lib.pk_survey_destroy(None) == pk.PK_OK
+    assert lib.pk_survey_launch_count(None) == 0
