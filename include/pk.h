@@ -424,7 +424,8 @@ typedef struct {
     double zmax;            /* largest redshift of the distance table (sky input);
                                0 selects 5                                      */
     double p0_fkp;          /* > 0: w_fkp = 1 / (1 + nbar P0); 0: given w_fkp    */
-    int max_batch;          /* Y_lm-weighted meshes per cuFFT call; 0: as many as
+    int max_batch;          /* Y_lm-weighted meshes held at once (one weighting
+                               pass and one bin pass per batch); 0: as many as
                                fit in half the free device memory                */
     int64_t capacity;       /* data + randoms objects to reserve (0: on demand)  */
 } pk_survey_config;
@@ -451,8 +452,7 @@ typedef struct {
 void pk_survey_config_default(pk_survey_config *cfg);
 
 /* Create a survey plan: validates cfg, allocates two catalogs' meshes, the
- * A_0 transform, the Y_lm-weighted meshes of one cuFFT batch and the cuFFT
- * plans, tabulates chi(z) when omega_m > 0, and computes the mode counts and
+ * A_0 transform, the Y_lm-weighted meshes of one batch and the cuFFT plans, tabulates chi(z) when omega_m > 0, and computes the mode counts and
  * mean k of the k bins.  All work runs on `cuda_stream`.  Errors: PK_EINVAL
  * (message through pk_plan_error), PK_ENOMEM, PK_ECUDA, PK_ECUFFT; on error
  * *out is NULL. */

@@ -616,8 +616,10 @@ def survey_catalog(pos, coord="cartesian", wcomp=None, wfkp=None, nbar=None) -> 
     ptr, code, n = _array_info(pos)
     if code == PK_F32X4:
         raise ValueError("survey positions must have shape (n, 3)")
-    return pk_survey_catalog(ptr, code, {"cartesian": PK_COORD_CARTESIAN, "sky": PK_COORD_SKY}[coord],
-                             _ptr_f32(wcomp, n, "wcomp"), _ptr_f32(wfkp, n, "wfkp"), _ptr_f32(nbar, n, "nbar"), n)
+    cat = pk_survey_catalog(ptr, code, {"cartesian": PK_COORD_CARTESIAN, "sky": PK_COORD_SKY}[coord],
+                            _ptr_f32(wcomp, n, "wcomp"), _ptr_f32(wfkp, n, "wfkp"), _ptr_f32(nbar, n, "nbar"), n)
+    cat._arrays = (pos, wcomp, wfkp, nbar)      # the struct holds raw pointers: keep the arrays alive
+    return cat
 
 
 def pk_survey_paint(plan, data: pk_survey_catalog, randoms: pk_survey_catalog | None = None):

@@ -15,7 +15,7 @@
 //            same / N^3 for the inverse), c2r -> the real field F.
 //            For each batch of Y_lm slots: k_survey_ylm writes F Y_lm(x^)
 //            (non-interlaced: F = D - alpha R on the fly, and the first batch
-//            also copies F for A_0), one batched r2c, k_survey_bin adds
+//            also copies F for A_0), one r2c per mesh, k_survey_bin adds
 //            h cw Y_lm(k^) Re[A_lm A_0^*] (and h cw |A_0|^2 once) into
 //            per-CTA FP64 rows; k_survey_final reduces the rows in a fixed
 //            order and normalizes.
@@ -51,26 +51,59 @@ constexpr int kConst = 16;              // constants block: see k_survey_const
 // Real spherical harmonics of the unit vector (x, y, z), orthonormal on the
 // sphere: Y_lm = N_lm P_l^|m|(z) (cos m phi or sin |m| phi) written as
 // polynomials in x, y, z, with N_lm from (2l + 1)/(4 pi) (l - |m|)!/(l + |m|)!
-// (times 2 for m != 0).
+// (times 2 for m != 0).  Slot s: 0..4 -> l = 2, m = s - 2; 5..13 -> l = 4,
+// m = s - 9.
+constexpr double kYa = 1.0925484305920792;    // (1/2) sqrt(15/pi)
+constexpr double kYb = 0.31539156525252005;   // (1/4) sqrt(5/pi)
+constexpr double kYc = 0.5462742152960396;    // (1/4) sqrt(15/pi)
+constexpr double kYd = 2.5033429417967046;    // (3/4) sqrt(35/pi)
+constexpr double kYe = 1.7701307697799304;    // (3/4) sqrt(35/(2 pi))
+constexpr double kYf = 0.9461746957575601;    // (3/4) sqrt(5/pi)
+constexpr double kYg = 0.6690465435572892;    // (3/4) sqrt(5/(2 pi))
+constexpr double kYh = 0.10578554691520431;   // (3/16) sqrt(1/pi)
+constexpr double kYi = 0.47308734787878004;   // (3/8) sqrt(5/pi)
+constexpr double kYj = 0.6258357354491761;    // (3/16) sqrt(35/pi)
+
 template <typename T>
 __host__ __device__ __forceinline__ T ylm_slot(int s, T x, T y, T z) {
     switch (s) {
-    case 0: return T(1.0925484305920792) * x * y;                          // l=2, m=-2
-    case 1: return T(1.0925484305920792) * y * z;                          // m=-1
-    case 2: return T(0.31539156525252005) * (T(3) * z * z - T(1));        // m=0
-    case 3: return T(1.0925484305920792) * x * z;                          // m=1
-    case 4: return T(0.5462742152960396) * (x * x - y * y);               // m=2
-    case 5: return T(2.5033429417967046) * x * y * (x * x - y * y);       // l=4, m=-4
-    case 6: return T(1.7701307697799304) * y * z * (T(3) * x * x - y * y);
-    case 7: return T(0.9461746957575601) * x * y * (T(7) * z * z - T(1));
-    case 8: return T(0.6690465435572892) * y * z * (T(7) * z * z - T(3));
-    case 9: return T(0.10578554691520431) * ((T(35) * z * z - T(30)) * z * z + T(3));
-    case 10: return T(0.6690465435572892) * x * z * (T(7) * z * z - T(3));
-    case 11: return T(0.47308734787878004) * (x * x - y * y) * (T(7) * z * z - T(1));
-    case 12: return T(1.7701307697799304) * x * z * (x * x - T(3) * y * y);
-    case 13: return T(0.6258357354491761) * (x * x * (x * x - T(3) * y * y) - y * y * (T(3) * x * x - y * y));
+    case 0: return T(kYa) * x * y;
+    case 1: return T(kYa) * y * z;
+    case 2: return T(kYb) * (T(3) * z * z - T(1));
+    case 3: return T(kYa) * x * z;
+    case 4: return T(kYc) * (x * x - y * y);
+    case 5: return T(kYd) * x * y * (x * x - y * y);
+    case 6: return T(kYe) * y * z * (T(3) * x * x - y * y);
+    case 7: return T(kYf) * x * y * (T(7) * z * z - T(1));
+    case 8: return T(kYg) * y * z * (T(7) * z * z - T(3));
+    case 9: return T(kYh) * ((T(35) * z * z - T(30)) * z * z + T(3));
+    case 10: return T(kYg) * x * z * (T(7) * z * z - T(3));
+    case 11: return T(kYi) * (x * x - y * y) * (T(7) * z * z - T(1));
+    case 12: return T(kYe) * x * z * (x * x - T(3) * y * y);
+    case 13: return T(kYj) * (x * x * (x * x - T(3) * y * y) - y * y * (T(3) * x * x - y * y));
     }
     return T(0);
+}
+
+// All 14 slots at once, sharing the products (the same polynomials).
+template <typename T>
+__device__ __forceinline__ void ylm_all(T x, T y, T z, T *Y) {
+    const T x2 = x * x, y2 = y * y, z2 = z * z, xy = x * y, yz = y * z, xz = x * z, d = x2 - y2;
+    const T t7 = T(7) * z2 - T(1), t3 = T(7) * z2 - T(3);
+    Y[0] = T(kYa) * xy;
+    Y[1] = T(kYa) * yz;
+    Y[2] = T(kYb) * (T(3) * z2 - T(1));
+    Y[3] = T(kYa) * xz;
+    Y[4] = T(kYc) * d;
+    Y[5] = T(kYd) * xy * d;
+    Y[6] = T(kYe) * yz * (T(3) * x2 - y2);
+    Y[7] = T(kYf) * xy * t7;
+    Y[8] = T(kYg) * yz * t3;
+    Y[9] = T(kYh) * ((T(35) * z2 - T(30)) * z2 + T(3));
+    Y[10] = T(kYg) * xz * t3;
+    Y[11] = T(kYi) * d * t7;
+    Y[12] = T(kYe) * xz * (x2 - T(3) * y2);
+    Y[13] = T(kYj) * (x2 * (x2 - T(3) * y2) - y2 * (T(3) * x2 - y2));
 }
 
 __host__ __device__ __forceinline__ int slot_ell(int s) { return s < 5 ? 2 : 4; }
@@ -293,16 +326,26 @@ k_survey_interlace(C *__restrict__ f1, const C *__restrict__ f2, C *__restrict__
     }
 }
 
+template <typename T> struct PairOf;
+template <> struct PairOf<float> { using type = float2; };
+template <> struct PairOf<double> { using type = double2; };
+
 // Y_lm-weighted copies of the real field: out[s][cell] = F(cell) Y_{s0+s}(x^).
 // FKP: F = D - alpha R read from the two catalogs' meshes (else F = D).
-// a0: if not NULL, F is also copied there (real layout) for A_0.
-template <typename T, bool FKP>
+// a0: if not NULL, F is also copied there (real layout) for A_0.  Two cells
+// per lane and two such pairs per step, loads first; rows are written whole,
+// padding pair included (as zeros), so the stores stream without partial
+// sectors.  NB > 0: the slots [S0, S0 + NB) fixed at compile time; NB = 0:
+// s0, nb.
+template <typename T, bool FKP, int S0, int NB>
 __global__ void __launch_bounds__(kRowThreads)
 k_survey_ylm(const T *__restrict__ D, const T *__restrict__ Rm, const double *__restrict__ c, T *__restrict__ a0,
              T *__restrict__ out, long long stride, int s0, int nb, int N, int rowlen, T ox, T oy, T oz, T H) {
+    using T2 = typename PairOf<T>::type;
     const T alpha = FKP ? (T)c[0] : (T)0;
     const long long rows = (long long)N * N;
     const int lane = threadIdx.x & 31;
+    const int npair = N / 2, nrow = rowlen / 2;     // pairs with cells, pairs per stored row
     const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long row = w0; row < rows; row += nw) {
@@ -310,24 +353,65 @@ k_survey_ylm(const T *__restrict__ D, const T *__restrict__ Rm, const double *__
         const T x = ox + (T)i * H, y = oy + (T)j * H;
         const T rxy = x * x + y * y;
         const long long base = row * rowlen;
-        for (int l = lane; l < N; l += 32) {
-            const long long idx = base + l;
-            T f = __ldcs(D + idx);
-            if (FKP) f -= alpha * __ldcs(Rm + idx);
-            if (a0) a0[idx] = f;
-            const T z = oz + (T)l * H;
-            const T r2 = rxy + z * z;
-            T ux = (T)0, uy = (T)0, uz = (T)0, g = (T)0;
-            if (r2 > (T)0) {
-                T inv;
-                if constexpr (sizeof(T) == 4) inv = rsqrtf(r2);
-                else inv = (T)1 / sqrt(r2);
-                ux = x * inv;
-                uy = y * inv;
-                uz = z * inv;
-                g = f;
+        for (int q0 = lane; q0 < nrow; q0 += 64) {
+            T2 f[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q = q0 + 32 * h;
+                f[h].x = (T)0;
+                f[h].y = (T)0;
+                if (q < npair) {
+                    f[h] = __ldcs(reinterpret_cast<const T2 *>(D + base + 2 * q));
+                    if (FKP) {
+                        const T2 r = __ldcs(reinterpret_cast<const T2 *>(Rm + base + 2 * q));
+                        f[h].x -= alpha * r.x;
+                        f[h].y -= alpha * r.y;
+                    }
+                }
             }
-            for (int s = 0; s < nb; ++s) out[(long long)s * stride + idx] = g * ylm_slot<T>(s0 + s, ux, uy, uz);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q = q0 + 32 * h;
+                if (q >= nrow) break;
+                const long long idx = base + 2 * q;
+                if (a0) *reinterpret_cast<T2 *>(a0 + idx) = f[h];
+                T u[2][3], g[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const T z = oz + (T)(2 * q + e) * H;
+                    const T r2 = rxy + z * z;
+                    u[e][0] = u[e][1] = u[e][2] = (T)0;
+                    g[e] = (T)0;
+                    if (q < npair && r2 > (T)0) {
+                        T inv;
+                        if constexpr (sizeof(T) == 4) inv = rsqrtf(r2);
+                        else inv = (T)1 / sqrt(r2);
+                        u[e][0] = x * inv;
+                        u[e][1] = y * inv;
+                        u[e][2] = z * inv;
+                        g[e] = e == 0 ? f[h].x : f[h].y;
+                    }
+                }
+                if constexpr (NB > 0) {
+                    T Y0[kSlots], Y1[kSlots];
+                    ylm_all<T>(u[0][0], u[0][1], u[0][2], Y0);
+                    ylm_all<T>(u[1][0], u[1][1], u[1][2], Y1);
+#pragma unroll
+                    for (int s = 0; s < NB; ++s) {
+                        T2 o;
+                        o.x = g[0] * Y0[S0 + s];
+                        o.y = g[1] * Y1[S0 + s];
+                        __stcs(reinterpret_cast<T2 *>(out + (long long)s * stride + idx), o);
+                    }
+                } else {
+                    for (int s = 0; s < nb; ++s) {
+                        T2 o;
+                        o.x = g[0] * ylm_slot<T>(s0 + s, u[0][0], u[0][1], u[0][2]);
+                        o.y = g[1] * ylm_slot<T>(s0 + s, u[1][0], u[1][1], u[1][2]);
+                        __stcs(reinterpret_cast<T2 *>(out + (long long)s * stride + idx), o);
+                    }
+                }
+            }
         }
     }
 }
@@ -335,8 +419,9 @@ k_survey_ylm(const T *__restrict__ D, const T *__restrict__ Rm, const double *__
 // Per-mode sums of one batch: hist[b] += h cw |A_0|^2 (first batch only),
 // hist[nk + b] / hist[2 nk + b] += h cw sum_s Y_s(k^) Re[A_s A_0^*] over the
 // batch's l = 2 / l = 4 slots.  Each CTA adds its histogram into its own FP64
-// row of `partial` (the first batch overwrites).
-template <typename R, typename C>
+// row of `partial` (the first batch overwrites).  NB > 0: slots [S0, S0 + NB)
+// fixed at compile time; NB = 0: s0, nb.
+template <typename R, typename C, int S0, int NB>
 __global__ void __launch_bounds__(kRowThreads)
 k_survey_bin(const C *__restrict__ A0, const C *__restrict__ S, long long stride_c, int s0, int nb, int first,
              pk::BinGeom g, const R *__restrict__ cw, const int *__restrict__ kedge, double *__restrict__ partial) {
@@ -352,11 +437,8 @@ k_survey_bin(const C *__restrict__ A0, const C *__restrict__ S, long long stride
     const int lane = threadIdx.x & 31;
     const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    bool has2 = false, has4 = false;
-    for (int s = 0; s < nb; ++s) {
-        if (slot_ell(s0 + s) == 2) has2 = true;
-        else has4 = true;
-    }
+    const int sb = NB > 0 ? S0 : s0, ne = NB > 0 ? NB : nb;
+    const bool has2 = ne > 0 && sb < 5, has4 = ne > 0 && sb + ne > 5;
     for (long long row = w0; row < rows; row += nw) {
         const int i = (int)(row / N), j = (int)(row - (long long)i * N);
         const int ip = i < half ? i : i - N, jp = j < half ? j : j - N;
@@ -378,21 +460,32 @@ k_survey_bin(const C *__restrict__ A0, const C *__restrict__ S, long long stride
             while (b < nk - 1 && m >= e.y) e = sedge[++b];
             R w = rowcw * cw[l];
             if (l != 0 && l != half) w += w;
-            const C a = A0[base + l];
+            const C a = __ldcs(A0 + base + l);
             if (first) atomicAdd(hist + b, w * (a.x * a.x + a.y * a.y));
-            if (nb > 0) {
-                const R kx = (R)ip * rs, ky = (R)jp * rs, kz = (R)l * rs;
-                R t2 = (R)0, t4 = (R)0;
+            if (ne == 0) continue;
+            const R kx = (R)ip * rs, ky = (R)jp * rs, kz = (R)l * rs;
+            R t2 = (R)0, t4 = (R)0;
+            if constexpr (NB > 0) {
+                R Y[kSlots];
+                ylm_all<R>(kx, ky, kz, Y);
+#pragma unroll
+                for (int s = 0; s < NB; ++s) {
+                    const C v = __ldcs(S + (long long)s * stride_c + base + l);
+                    const R re = v.x * a.x + v.y * a.y;
+                    if (S0 + s < 5) t2 += Y[S0 + s] * re;
+                    else t4 += Y[S0 + s] * re;
+                }
+            } else {
                 for (int s = 0; s < nb; ++s) {
-                    const C v = S[(long long)s * stride_c + base + l];
+                    const C v = __ldcs(S + (long long)s * stride_c + base + l);
                     const R re = v.x * a.x + v.y * a.y;
                     const R y = ylm_slot<R>(s0 + s, kx, ky, kz);
-                    if (slot_ell(s0 + s) == 2) t2 += y * re;
+                    if (s0 + s < 5) t2 += y * re;
                     else t4 += y * re;
                 }
-                if (has2) atomicAdd(hist + nk + b, w * t2);
-                if (has4) atomicAdd(hist + 2 * nk + b, w * t4);
             }
+            if (has2) atomicAdd(hist + nk + b, w * t2);
+            if (has4) atomicAdd(hist + 2 * nk + b, w * t4);
         }
     }
     __syncthreads();
@@ -436,11 +529,11 @@ struct pk_survey_s {
     size_t esz = 4;
     long long mesh_reals = 0;
     int sa = 0, sb = 0;             // active Y_lm slots [sa, sb)
-    int batch = 0;                  // slots per cuFFT call
+    int batch = 0;                  // Y_lm-weighted meshes resident per pass
     void *a0 = nullptr;             // A_0: one mesh (complex half grid)
     void *slots = nullptr;          // batch meshes
-    cufftHandle fft_b = 0, fft_t = 0, fft_inv = 0;
-    int have_b = 0, have_t = 0, have_inv = 0, tail = 0;
+    cufftHandle fft_b = 0, fft_inv = 0;   // single-mesh r2c, single-mesh c2r
+    int have_b = 0, have_inv = 0;
     void *fft_work = nullptr;
     void *obj = nullptr;            // staged box-frame objects (data then randoms)
     int64_t obj_cap = 0;
@@ -522,7 +615,6 @@ void free_survey(pk_survey_s *S) {
     if (!S) return;
     if (S->st || S->P) cudaStreamSynchronize(S->st);
     if (S->have_b) cufftDestroy(S->fft_b);
-    if (S->have_t) cufftDestroy(S->fft_t);
     if (S->have_inv) cufftDestroy(S->fft_inv);
     void *dev[] = {S->a0, S->slots, S->fft_work, S->obj, S->stage, S->chi, S->psum, S->cst, S->partial, S->res};
     for (void *d : dev)
@@ -667,18 +759,19 @@ static pk_status survey_build(pk_survey_s *S, const pk_survey_config *cfg, void 
         SV_CUDA(S, cudaMemcpy(S->chi, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice));
     }
 
-    // batch of Y_lm-weighted meshes per cuFFT call
+    // Y_lm-weighted meshes resident per pass (written by one field pass, read
+    // by one bin pass); each is transformed by its own single-mesh cuFFT call
+    // (at 1024^3 a batched plan over 14 meshes measured 2x slower per mesh).
     if (nslot > 0) {
         int batch = nslot;
         if (c.max_batch > 0) batch = std::min(batch, c.max_batch);
         else {
             size_t fr = 0, tot = 0;
             SV_CUDA(S, cudaMemGetInfo(&fr, &tot));
-            const size_t fit = fr / 2 / (2 * mesh_bytes);
+            const size_t fit = fr / 2 / mesh_bytes;
             batch = (int)std::max<size_t>(1, std::min<size_t>((size_t)batch, fit));
         }
         S->batch = batch;
-        S->tail = nslot % batch;
         SV_CUDA(S, cudaMalloc(&S->slots, mesh_bytes * (size_t)batch));
         long long n[3] = {S->N, S->N, S->N};
         long long inembed[3] = {S->N, S->N, 2LL * S->Nh};
@@ -688,16 +781,8 @@ static pk_status survey_build(pk_survey_s *S, const pk_survey_config *cfg, void 
         S->have_b = 1;
         SV_CUFFT(S, cufftSetAutoAllocation(S->fft_b, 0));
         SV_CUFFT(S, cufftMakePlanMany64(S->fft_b, 3, n, inembed, 1, S->mesh_reals, onembed, 1, S->mesh_reals / 2,
-                                        S->f64 ? CUFFT_D2Z : CUFFT_R2C, batch, &w1));
+                                        S->f64 ? CUFFT_D2Z : CUFFT_R2C, 1, &w1));
         work = std::max(work, w1);
-        if (S->tail) {
-            SV_CUFFT(S, cufftCreate(&S->fft_t));
-            S->have_t = 1;
-            SV_CUFFT(S, cufftSetAutoAllocation(S->fft_t, 0));
-            SV_CUFFT(S, cufftMakePlanMany64(S->fft_t, 3, n, inembed, 1, S->mesh_reals, onembed, 1,
-                                            S->mesh_reals / 2, S->f64 ? CUFFT_D2Z : CUFFT_R2C, S->tail, &w1));
-            work = std::max(work, w1);
-        }
         if (c.interlaced) {
             SV_CUFFT(S, cufftCreate(&S->fft_inv));
             S->have_inv = 1;
@@ -707,9 +792,9 @@ static pk_status survey_build(pk_survey_s *S, const pk_survey_config *cfg, void 
             work = std::max(work, w1);
         }
         SV_CUDA(S, cudaMalloc(&S->fft_work, std::max<size_t>(work, 16)));
-        cufftHandle hs[3] = {S->fft_b, S->fft_t, S->fft_inv};
-        int have[3] = {S->have_b, S->have_t, S->have_inv};
-        for (int k = 0; k < 3; ++k) {
+        cufftHandle hs[2] = {S->fft_b, S->fft_inv};
+        int have[2] = {S->have_b, S->have_inv};
+        for (int k = 0; k < 2; ++k) {
             if (!have[k]) continue;
             SV_CUFFT(S, cufftSetWorkArea(hs[k], S->fft_work));
             SV_CUFFT(S, cufftSetStream(hs[k], S->st));
@@ -927,21 +1012,40 @@ static pk_status survey_compute_t(pk_survey_s *S) {
     const pk::BinGeom &g = P->bg;
     const size_t smem = ((3 * (size_t)g.nk * sizeof(R) + 15) / 16) * 16 + (size_t)g.nk * sizeof(int2);
     if (smem > 200 * 1024) return sfail(S, PK_EINVAL, "too many k bins for the per-CTA histogram");
-    SV_CUDA(S, cudaFuncSetAttribute(k_survey_bin<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+        void (*bins[4])(const C *, const C *, long long, int, int, int, pk::BinGeom, const R *, const int *,
+                        double *) = {k_survey_bin<R, C, 0, 0>, k_survey_bin<R, C, 0, 14>, k_survey_bin<R, C, 0, 5>,
+                                     k_survey_bin<R, C, 5, 9>};
+        for (auto f : bins)
+            SV_CUDA(S, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
     const int nbatches = nslot > 0 ? (nslot + S->batch - 1) / S->batch : 1;
     for (int bi = 0; bi < nbatches; ++bi) {
         const int s0 = S->sa + bi * S->batch;
         const int nb = nslot > 0 ? std::min(S->batch, S->sb - s0) : 0;
         const bool first = bi == 0;
         R *a0copy = (!il && first) ? A0r : nullptr;
+        // compile-time slot ranges for the usual batches, else the generic kernel
+        const int spec = (s0 == 0 && nb == 14) ? 1 : (s0 == 0 && nb == 5) ? 2 : (s0 == 5 && nb == 9) ? 3 : 0;
         if (nb > 0 || a0copy) {
             SV_CUDA(S, tmark(S, 1, PK_SURVEY_STAGE_FIELD));
-            if (il)
-                k_survey_ylm<R, false><<<rowblocks, kRowThreads, 0, st>>>(D, nullptr, S->cst, nullptr, SL, mr, s0, nb,
-                                                                          N, 2 * Nh, ox, oy, oz, H);
-            else
-                k_survey_ylm<R, true><<<rowblocks, kRowThreads, 0, st>>>(D, Rm, S->cst, a0copy, SL, mr, s0, nb, N,
-                                                                         2 * Nh, ox, oy, oz, H);
+            const R *Rsrc = il ? nullptr : Rm;
+            R *a0dst = il ? nullptr : a0copy;
+#define SV_YLM(FKP, S0_, NB_)                                                                                   \
+    k_survey_ylm<R, FKP, S0_, NB_><<<rowblocks, kRowThreads, 0, st>>>(D, Rsrc, S->cst, a0dst, SL, mr, s0, nb, N, \
+                                                                      2 * Nh, ox, oy, oz, H)
+            if (il) {
+                if (spec == 1) SV_YLM(false, 0, 14);
+                else if (spec == 2) SV_YLM(false, 0, 5);
+                else if (spec == 3) SV_YLM(false, 5, 9);
+                else SV_YLM(false, 0, 0);
+            } else {
+                if (spec == 1) SV_YLM(true, 0, 14);
+                else if (spec == 2) SV_YLM(true, 0, 5);
+                else if (spec == 3) SV_YLM(true, 5, 9);
+                else SV_YLM(true, 0, 0);
+            }
+#undef SV_YLM
             SV_CUDA(S, cudaGetLastError());
             S->launches += 1;
         }
@@ -955,19 +1059,26 @@ static pk_status survey_compute_t(pk_survey_s *S) {
                                          reinterpret_cast<cufftComplex *>(A0r)));
             }
         }
-        if (nb > 0) {
-            cufftHandle h = nb == S->batch ? S->fft_b : S->fft_t;
+        for (int k = 0; k < nb; ++k) {
+            R *mk = SL + (long long)k * mr;
             if (S->f64) {
-                SV_CUFFT(S, cufftExecD2Z(h, reinterpret_cast<cufftDoubleReal *>(SL),
-                                         reinterpret_cast<cufftDoubleComplex *>(SL)));
+                SV_CUFFT(S, cufftExecD2Z(S->fft_b, reinterpret_cast<cufftDoubleReal *>(mk),
+                                         reinterpret_cast<cufftDoubleComplex *>(mk)));
             } else {
-                SV_CUFFT(S, cufftExecR2C(h, reinterpret_cast<cufftReal *>(SL), reinterpret_cast<cufftComplex *>(SL)));
+                SV_CUFFT(S, cufftExecR2C(S->fft_b, reinterpret_cast<cufftReal *>(mk), reinterpret_cast<cufftComplex *>(mk)));
             }
         }
         SV_CUDA(S, tmark(S, 1, PK_SURVEY_STAGE_BIN));
-        k_survey_bin<R, C><<<S->Gb, kRowThreads, smem, st>>>(A0, reinterpret_cast<const C *>(SL), mr / 2, s0, nb,
-                                                              first ? 1 : 0, g, reinterpret_cast<const R *>(P->d_cw),
-                                                              P->d_kedge, S->partial);
+#define SV_BIN(S0_, NB_)                                                                                        \
+    k_survey_bin<R, C, S0_, NB_><<<S->Gb, kRowThreads, smem, st>>>(A0, reinterpret_cast<const C *>(SL), mr / 2, s0, \
+                                                                   nb, first ? 1 : 0, g,                            \
+                                                                   reinterpret_cast<const R *>(P->d_cw), P->d_kedge, \
+                                                                   S->partial)
+        if (spec == 1) SV_BIN(0, 14);
+        else if (spec == 2) SV_BIN(0, 5);
+        else if (spec == 3) SV_BIN(5, 9);
+        else SV_BIN(0, 0);
+#undef SV_BIN
         SV_CUDA(S, cudaGetLastError());
         S->launches += 1;
     }
