@@ -232,6 +232,9 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
     const double kmax = c.kmax > 0.0 ? c.kmax : (M_PI * P->N) / L;
     const double nkd = floor((kmax - c.kmin) / c.dk);
     if (!(nkd >= 1.0) || nkd > 1e6) return fail(P, PK_EINVAL, "k binning gives no bins (or more than 1e6)");
+    // The bin kernel's FP32 estimate of the k bin must stay within one bin of
+    // the exact FP64 bin (its absolute error is below 4e-7 kmax / dk + 0.1).
+    if (kmax / c.dk >= 1048576.0) return fail(P, PK_EINVAL, "k binning too fine: kmax / dk must be below 2^20");
     const int nk = (int)nkd;
     PK_CUDA(P, cudaGetDevice(&P->device));
     PK_CUDA(P, cudaDeviceGetAttribute(&P->nsm, cudaDevAttrMultiProcessorCount, P->device));

@@ -927,37 +927,39 @@ __device__ __forceinline__ C cmul(C a, C b) {
     return r;
 }
 
-__device__ __forceinline__ void load_vec(const float2 *p, float2 *a) {
-#pragma unroll
-    for (int k = 0; k < kBinVec / 2; ++k) {
-        const float4 u = __ldcs(reinterpret_cast<const float4 *>(p) + k);
-        a[2 * k] = make_float2(u.x, u.y);
-        a[2 * k + 1] = make_float2(u.z, u.w);
-    }
-}
-__device__ __forceinline__ void load_vec(const double2 *p, double2 *a) {
-#pragma unroll
-    for (int k = 0; k < kBinVec; ++k) a[k] = __ldcs(p + k);
-}
-
 __host__ __device__ __forceinline__ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 template <typename R, typename C, typename A>
 struct BinSmem {
     // layout: hist[nh] (A), cw_l[Nh] (R), ph_l[Nh] (C), edge pairs[nk] (int2: m range of bin b)
     __host__ __device__ static size_t off_cw(const BinGeom &g) { return align_up((size_t)g.nh * sizeof(A), 16); }
-    __host__ __device__ static size_t off_ph(const BinGeom &g) { return align_up(off_cw(g) + (size_t)g.Nh * sizeof(R), 16); }
-    __host__ __device__ static size_t off_edge(const BinGeom &g) { return align_up(off_ph(g) + (size_t)g.Nh * sizeof(C), 16); }
+    // the cw and ph tables hold Nh + Nh/4 + 1 entries: k_bin stores entry l at l + l/4
+    __host__ __device__ static size_t tab(const BinGeom &g) { return (size_t)g.Nh + (size_t)(g.Nh >> 2) + 1; }
+    __host__ __device__ static size_t off_ph(const BinGeom &g) { return align_up(off_cw(g) + tab(g) * sizeof(R), 16); }
+    __host__ __device__ static size_t off_edge(const BinGeom &g) { return align_up(off_ph(g) + tab(g) * sizeof(C), 16); }
     __host__ __device__ static size_t bytes(const BinGeom &g) { return align_up(off_edge(g) + (size_t)g.nk * sizeof(int2), 16); }
 };
 
-// CROSS: the meshes of a second catalog at meshb; each mode contributes
-// Re(delta_a conj(delta_b)) instead of |delta|^2.
-template <bool IL, bool TWOD, bool POLES, typename R, typename C, typename A, bool CROSS = false>
-__global__ void __launch_bounds__(kBinThreads)
-k_bin(const C *__restrict__ mesh, long long item_stride_c, long long mesh_stride_c, int nchunks,
-      BinGeom g, const R *__restrict__ cw, const C *__restrict__ ph, const int *__restrict__ kedge,
-      A *__restrict__ partial, const C *__restrict__ meshb) {
+// floor(sqrt(x)) for 0 <= x < 2^26, exact.
+__device__ __forceinline__ int isqrt_floor(int x) {
+    int s = (int)sqrtf((float)x);
+    while (s > 0 && s * s > x) --s;
+    while ((s + 1) * (s + 1) <= x) ++s;
+    return s;
+}
+
+// Fused compensate + interlace + bin.  Rows are the unit of work: each warp
+// takes whole rows (i, j) and visits only the l range whose modes fall in a k
+// bin, mlo <= i'^2 + j'^2 + l^2 < mhi (and m != 0); each lane sums kBinVec
+// consecutive modes of it in registers and flushes a run to the per-CTA
+// shared histogram when its bin changes.  CROSS: the meshes of a second
+// catalog at meshb; each mode contributes Re(delta_a conj(delta_b)) instead
+// of |delta|^2.  MU32: the mu-bin test q^2 m <= nmu^2 l^2 fits in 32 bits.
+template <bool IL, bool TWOD, bool POLES, typename R, typename C, typename A, bool CROSS = false, bool MU32 = true>
+__global__ void __launch_bounds__(kBinThreads, sizeof(R) == 4 ? 2 : 1)
+k_bin(const C *__restrict__ mesh, long long item_stride_c, long long mesh_stride_c, BinGeom g,
+      const R *__restrict__ cw, const C *__restrict__ ph, const int *__restrict__ kedge, A *__restrict__ partial,
+      const C *__restrict__ meshb) {
     using SM = BinSmem<R, C, A>;
     extern __shared__ __align__(16) unsigned char smraw[];
     A *hist = reinterpret_cast<A *>(smraw);
@@ -965,9 +967,11 @@ k_bin(const C *__restrict__ mesh, long long item_stride_c, long long mesh_stride
     C *sph = reinterpret_cast<C *>(smraw + SM::off_ph(g));
     int2 *sedge = reinterpret_cast<int2 *>(smraw + SM::off_edge(g));
     for (int k = threadIdx.x; k < g.nh; k += blockDim.x) hist[k] = (A)0;
+    // entry l at l + l/4: lanes read l = l0 + 4 lane + v, which this skew
+    // spreads over all banks (4-byte cw) or two wavefronts (8-byte ph)
     for (int k = threadIdx.x; k < g.Nh; k += blockDim.x) {
-        scw[k] = cw[k];
-        sph[k] = ph[k + g.N / 2];
+        scw[k + (k >> 2)] = cw[k];
+        sph[k + (k >> 2)] = ph[k + g.N / 2];
     }
     for (int k = threadIdx.x; k < g.nk; k += blockDim.x) sedge[k] = make_int2(kedge[k], kedge[k + 1]);
     __syncthreads();
@@ -977,157 +981,123 @@ k_bin(const C *__restrict__ mesh, long long item_stride_c, long long mesh_stride
     const C *m2 = m1 + mesh_stride_c;
     const C *n1 = CROSS ? meshb : m1;
     const C *n2 = n1 + mesh_stride_c;
-    const long long CH = (long long)kBinThreads * kBinVec;
-    const int half = g.N / 2;
-    const int Nh = g.Nh;
-    // Start of this CTA's first chunk as (row, l); advanced by gridDim.x
-    // chunks per iteration without 64-bit division.
-    int row_base, l_base;
-    {
-        const long long f = (long long)blockIdx.x * CH;
-        row_base = (int)(f / Nh);
-        l_base = (int)(f - (long long)row_base * Nh);
-    }
-    const long long step = (long long)gridDim.x * CH;
-    const int step_rows = (int)(step / Nh), step_l = (int)(step - (long long)step_rows * Nh);
-    for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
-        const long long f0 = (long long)chunk * CH + (long long)kBinVec * threadIdx.x;
-        if (f0 < g.modes) {
-            // (row, l) of f0: l_base + 8 tid = drow Nh + l with a float-reciprocal quotient
-            const int lt = l_base + kBinVec * (int)threadIdx.x;
-            int drow = (int)((float)lt * g.inv_Nh);
-            int l = lt - drow * Nh;
-            if (l < 0) { --drow; l += Nh; }
-            if (l >= Nh) { ++drow; l -= Nh; }
-            const int row = row_base + drow;
-            int i = (int)((float)row * g.inv_N);
-            int j = row - i * g.N;
-            if (j < 0) { --i; j += g.N; }
-            if (j >= g.N) { ++i; j -= g.N; }
-            int r2 = 0;
-            R rowcw = (R)0;
-            C rowph;
-            rowph.x = (R)0;
-            rowph.y = (R)0;
-            auto row_terms = [&]() {
-                const int ip = i < half ? i : i - g.N;
-                const int jp = j < half ? j : j - g.N;
-                r2 = ip * ip + jp * jp;
-                rowcw = cw[i] * cw[j];
-                if (IL) {
-                    rowcw *= (R)0.25;
-                    rowph = cmul(ph[ip + half], ph[jp + half]);
-                }
-            };
-            row_terms();
-            // Skip (without loading) a run of modes that lies wholly outside
-            // [mlo, mhi): m grows with l inside a row.
-            if (l + kBinVec <= Nh) {
-                const int mlast = r2 + (l + kBinVec - 1) * (l + kBinVec - 1);
-                if (r2 + l * l >= g.mhi || mlast < g.mlo) goto next_chunk;
-            }
+    const int half = g.N / 2, N = g.N, Nh = g.Nh;
+    const int nk = g.nk, nmu = g.nmu, hbase = g.hbase;
+    const float kscale = g.kscale, koff = g.koff;
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int rows = N * N;
+    for (int row = blockIdx.x * wpb + (threadIdx.x >> 5); row < rows; row += gridDim.x * wpb) {
+        const int i = row / N, j = row - i * N;
+        const int ip = i < half ? i : i - N;
+        const int jp = j < half ? j : j - N;
+        const int r2 = ip * ip + jp * jp;
+        if (r2 >= g.mhi) continue;
+        const int lhi = min(Nh, isqrt_floor(g.mhi - 1 - r2) + 1);
+        int llo = g.mlo > r2 ? isqrt_floor(g.mlo - r2 - 1) + 1 : 0;
+        if (r2 == 0 && llo == 0) llo = 1;
+        if (llo >= lhi) continue;
+        R rowcw = cw[i] * cw[j];
+        C rowph;
+        rowph.x = (R)0;
+        rowph.y = (R)0;
+        if (IL) {
+            rowcw *= (R)0.25;
+            rowph = cmul(ph[ip + half], ph[jp + half]);
+        }
+        const long long base = (long long)row * Nh;
+        for (int l0 = llo + kBinVec * lane; l0 < lhi; l0 += 32 * kBinVec) {
+            const int cnt = lhi - l0;                   // modes of this run: min(cnt, kBinVec)
             C a[kBinVec], b2[kBinVec], ca[CROSS ? kBinVec : 1], cb2[CROSS && IL ? kBinVec : 1];
-            load_vec(m1 + f0, a);
-            if (IL) load_vec(m2 + f0, b2);
-            if (CROSS) {
-                load_vec(n1 + f0, ca);
-                if (IL) load_vec(n2 + f0, cb2);
+#pragma unroll
+            for (int v = 0; v < kBinVec; ++v) {
+                const long long at = base + l0 + min(v, cnt - 1);   // the tail re-reads the last mode
+                a[v] = __ldcs(m1 + at);
+                if (IL) b2[v] = __ldcs(m2 + at);
+                if (CROSS) {
+                    ca[CROSS ? v : 0] = __ldcs(n1 + at);
+                    if (IL) cb2[CROSS && IL ? v : 0] = __ldcs(n2 + at);
+                }
             }
             int cur2 = -1, cur1 = -1;                 // open register runs
             R run2 = (R)0, runm2 = (R)0, runm4 = (R)0;
 #pragma unroll
             for (int v = 0; v < kBinVec; ++v) {
-                if (l == Nh) {
-                    l = 0;
-                    if (++j == g.N) {
-                        j = 0;
-                        ++i;
-                    }
-                    row_terms();
-                }
+                const bool live = v < cnt;
+                const int l = min(l0 + v, lhi - 1);
                 const int m = r2 + l * l;
-                if (m != 0 && m >= g.mlo && m < g.mhi) {
-                    const float rsm = rsqrtf((float)m);
-                    int b = (int)((float)m * rsm * g.kscale - g.koff);   // estimate, then exact
-                    b = min(max(b, 0), g.nk - 1);
-                    int2 e = sedge[b];
-                    while (b > 0 && m < e.x) e = sedge[--b];
-                    while (b < g.nk - 1 && m >= e.y) e = sedge[++b];
-                    C z = a[v];
-                    C y;
-                    if (CROSS) y = ca[CROSS ? v : 0];
-                    if (IL) {
-                        const C t = cmul(rowph, sph[l]);
-                        z.x += b2[v].x * t.x - b2[v].y * t.y;
-                        z.y += b2[v].x * t.y + b2[v].y * t.x;
-                        if (CROSS) {
-                            const C u = cb2[CROSS && IL ? v : 0];
-                            y.x += u.x * t.x - u.y * t.y;
-                            y.y += u.x * t.y + u.y * t.x;
-                        }
-                    }
-                    R pw = (CROSS ? z.x * y.x + z.y * y.y : z.x * z.x + z.y * z.y) * rowcw * scw[l];
-                    if (l != 0 && l != half) pw += pw;
-                    int key = b;
-                    if (TWOD) {
-                        const int nmu = g.nmu;
-                        int q = (int)((float)(nmu * l) * rsm);
-                        q = min(max(q, 0), nmu - 1);
-                        if (g.mu32) {             // q^2 m and nmu^2 l^2 fit in 32 bits
-                            const unsigned rhs = (unsigned)(nmu * nmu) * (unsigned)(l * l);
-                            while (q > 0 && (unsigned)(q * q) * (unsigned)m > rhs) --q;
-                            while (q < nmu - 1 && (unsigned)((q + 1) * (q + 1)) * (unsigned)m <= rhs) ++q;
-                        } else {
-                            const long long rhs = (long long)nmu * nmu * l * l;
-                            while (q > 0 && (long long)q * q * m > rhs) --q;
-                            while (q < nmu - 1 && (long long)(q + 1) * (q + 1) * m <= rhs) ++q;
-                        }
-                        key = b * nmu + q;
-                    }
-                    if (key != cur2) {
-                        if (cur2 >= 0) atomicAdd(hist + cur2, (A)run2);
-                        cur2 = key;
-                        run2 = (R)0;
-                    }
-                    run2 += pw;
-                    if (POLES) {
-                        if (b != cur1) {
-                            if (cur1 >= 0) {
-                                atomicAdd(hist + g.hbase + cur1, (A)runm2);
-                                atomicAdd(hist + g.hbase + g.nk + cur1, (A)runm4);
-                            }
-                            cur1 = b;
-                            runm2 = (R)0;
-                            runm4 = (R)0;
-                        }
-                        // FP32: mu = l rsqrt(m) from the k-bin estimate (a few ulp);
-                        // FP64: the exact quotient
-                        R mu2;
-                        if (sizeof(R) == 4) {
-                            const float mu = (float)l * rsm;
-                            mu2 = (R)(mu * mu);
-                        } else {
-                            mu2 = (R)(l * l) / (R)m;
-                        }
-                        const R t2 = pw * mu2;
-                        runm2 += t2;
-                        runm4 += t2 * mu2;
+                // FP32 estimate of the k bin, then one exact step against the FP64
+                // edges: the estimate's error (below 4e-7 kmax / dk + 0.1, the
+                // plan requires kmax / dk < 2^20) puts it at most one bin off
+                const float rsm = rsqrtf((float)m);
+                int b = (int)((float)m * rsm * kscale - koff);
+                b = min(max(b, 0), nk - 1);
+                {
+                    const int2 e = sedge[b];
+                    b += (int)(m >= e.y) - (int)(m < e.x);
+                }
+                C z = a[v];
+                C y;
+                if (CROSS) y = ca[CROSS ? v : 0];
+                if (IL) {
+                    const C t = cmul(rowph, sph[l + (l >> 2)]);
+                    z.x += b2[v].x * t.x - b2[v].y * t.y;
+                    z.y += b2[v].x * t.y + b2[v].y * t.x;
+                    if (CROSS) {
+                        const C u = cb2[CROSS && IL ? v : 0];
+                        y.x += u.x * t.x - u.y * t.y;
+                        y.y += u.x * t.y + u.y * t.x;
                     }
                 }
-                ++l;
+                R pw = (CROSS ? z.x * y.x + z.y * y.y : z.x * z.x + z.y * z.y) * rowcw * scw[l + (l >> 2)];
+                pw *= (R)((l != 0 && l != half) ? 2 : 1) * (R)(live ? 1 : 0);
+                int key = b;
+                if (TWOD) {
+                    // mu bin: FP32 estimate, then one exact integer step each way
+                    int q = (int)((float)(nmu * l) * rsm);
+                    q = min(max(q, 0), nmu - 1);
+                    if (MU32) {
+                        const unsigned rhs = (unsigned)(nmu * nmu) * (unsigned)(l * l);
+                        q -= (int)(q > 0 && (unsigned)(q * q) * (unsigned)m > rhs);
+                        q += (int)(q < nmu - 1 && (unsigned)((q + 1) * (q + 1)) * (unsigned)m <= rhs);
+                    } else {
+                        const long long rhs = (long long)nmu * nmu * l * l;
+                        q -= (int)(q > 0 && (long long)q * q * m > rhs);
+                        q += (int)(q < nmu - 1 && (long long)(q + 1) * (q + 1) * m <= rhs);
+                    }
+                    key = b * nmu + q;
+                }
+                // flush an open run when the key changes (predicated, no branch)
+                const bool new2 = key != cur2;
+                if (new2 && cur2 >= 0) atomicAdd(hist + cur2, (A)run2);
+                run2 = new2 ? pw : run2 + pw;
+                cur2 = key;
+                if (POLES) {
+                    // FP32: mu = l rsqrt(m) from the k-bin estimate (a few ulp);
+                    // FP64: the exact quotient
+                    R mu2;
+                    if (sizeof(R) == 4) {
+                        const float mu = (float)l * rsm;
+                        mu2 = (R)(mu * mu);
+                    } else {
+                        mu2 = (R)(l * l) / (R)m;
+                    }
+                    const R t2 = pw * mu2;
+                    const bool new1 = b != cur1;
+                    if (new1 && cur1 >= 0) {
+                        atomicAdd(hist + hbase + cur1, (A)runm2);
+                        atomicAdd(hist + hbase + nk + cur1, (A)runm4);
+                    }
+                    runm2 = new1 ? t2 : runm2 + t2;
+                    runm4 = new1 ? t2 * mu2 : runm4 + t2 * mu2;
+                    cur1 = b;
+                }
             }
-            if (cur2 >= 0) atomicAdd(hist + cur2, (A)run2);
-            if (POLES && cur1 >= 0) {
-                atomicAdd(hist + g.hbase + cur1, (A)runm2);
-                atomicAdd(hist + g.hbase + g.nk + cur1, (A)runm4);
+            atomicAdd(hist + cur2, (A)run2);
+            if (POLES) {
+                atomicAdd(hist + hbase + cur1, (A)runm2);
+                atomicAdd(hist + hbase + nk + cur1, (A)runm4);
             }
-        }
-    next_chunk:
-        l_base += step_l;
-        row_base += step_rows;
-        if (l_base >= Nh) {
-            l_base -= Nh;
-            ++row_base;
         }
     }
     __syncthreads();
@@ -1557,14 +1527,13 @@ static cudaError_t bin_inst(const void *mesh, long long item_stride_c, long long
                             int nitems, int G, const BinGeom &g, const void *cw, const void *ph,
                             const int *kedge, void *partial, const void *meshb, cudaStream_t st) {
     const size_t smem = BinSmem<R, C, A>::bytes(g);
-    auto kern = k_bin<IL, TWOD, POLES, R, C, A, CROSS>;
+    auto kern = (g.mu32 || !TWOD) ? k_bin<IL, TWOD, POLES, R, C, A, CROSS, true>
+                                  : k_bin<IL, TWOD, POLES, R, C, A, CROSS, false>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    const long long CH = (long long)kBinThreads * kBinVec;
-    const int nchunks = (int)((g.modes + CH - 1) / CH);
     dim3 grid(G, nitems);
     kern<<<grid, kBinThreads, smem, st>>>(reinterpret_cast<const C *>(mesh), item_stride_c,
-                                          mesh_stride_c, nchunks, g, reinterpret_cast<const R *>(cw),
+                                          mesh_stride_c, g, reinterpret_cast<const R *>(cw),
                                           reinterpret_cast<const C *>(ph), kedge,
                                           reinterpret_cast<A *>(partial), reinterpret_cast<const C *>(meshb));
     return cudaGetLastError();

@@ -127,6 +127,7 @@ extern "C" pk_status pk_bin_static(const pk_config *cfg, const void *mesh, const
     const double kmax = c.kmax > 0.0 ? c.kmax : (M_PI * N) / L;
     const double nkd = floor((kmax - c.kmin) / c.dk);
     if (!(nkd >= 1.0) || nkd > kMaxBins) return static_fail(PK_EINVAL, "k binning gives no bins or more than 8192");
+    if (kmax / c.dk >= 1048576.0) return static_fail(PK_EINVAL, "k binning too fine: kmax / dk must be below 2^20");
     const int nk = (int)nkd;
     const int mcap = 3 * (N / 2) * (N / 2) + 1;
 

@@ -106,8 +106,6 @@ __device__ __forceinline__ void ylm_all(T x, T y, T z, T *Y) {
     Y[13] = T(kYj) * (x2 * (x2 - T(3) * y2) - y2 * (T(3) * x2 - y2));
 }
 
-__host__ __device__ __forceinline__ int slot_ell(int s) { return s < 5 ? 2 : 4; }
-
 // ---------------------------------------------------------------- prep --
 
 __device__ __forceinline__ double warp_sum(double v) {

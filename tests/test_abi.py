@@ -162,3 +162,12 @@ def test_survey_null_arguments(pk):
     assert lib.pk_survey_result(None, None) == pk.PK_EINVAL
     assert lib.pk_survey_destroy(None) == pk.PK_OK
     assert lib.pk_survey_launch_count(None) == 0
+
+
+def test_plan_rejects_too_fine_binning(pk):
+    """The bin kernel's FP32 bin estimate is exact to one bin only while
+    kmax / dk < 2^20."""
+    c = pk.make_config(1000.0, 64, "cic", kmin=0.19, kmax=0.2, dk=1e-7)
+    h = ctypes.c_void_p()
+    assert pk.load().pk_plan(ctypes.byref(c), None, ctypes.byref(h)) == pk.PK_EINVAL
+    assert "too fine" in pk.load().pk_plan_error().decode()
