@@ -463,6 +463,7 @@ pk_status pk_survey_plan(const pk_survey_config *cfg, void *cuda_stream, pk_surv
  * are taken in FP64, and both catalogs are painted into their own meshes
  * (int64 fixed point, as pk_paint).  randoms == NULL keeps the randoms
  * painted by the previous call (mocks that share one random catalog).
+ * With no data objects alpha and I are 0 and every P_l is NaN.
  * Objects outside the box wrap periodically and are counted in n_outside;
  * sky objects with z outside [0, zmax] (or NaN) get weight 0 and are counted
  * in n_rejected.  Asynchronous on the plan's stream; host arrays are copied

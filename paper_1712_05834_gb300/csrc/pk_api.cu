@@ -282,9 +282,6 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
     bg.koff = (float)(c.kmin / c.dk);
     bg.mlo = P->kedge[0];
     bg.mhi = P->kedge[nk];
-    bg.modes = (long long)P->N * P->N * P->Nh;
-    bg.inv_Nh = 1.0f / (float)P->Nh;
-    bg.inv_N = 1.0f / (float)P->N;
     bg.mu32 = (double)(nmu + 1) * (nmu + 1) * (double)(bg.mhi + 1) < 4294967295.0 &&
               (double)nmu * nmu * (double)(P->N / 2) * (P->N / 2) < 4294967295.0;
     if (bin_smem_bytes(bg, P->f64) > 200 * 1024)

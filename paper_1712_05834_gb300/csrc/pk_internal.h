@@ -37,8 +37,6 @@ struct BinGeom {
     int nh;                 // histogram length
     float kscale, koff;     // bin estimate: sqrt(m) * kscale - koff
     int mlo, mhi;           // binned modes have mlo <= m < mhi (and m != 0)
-    long long modes;        // stored modes per mesh: N * N * Nh
-    float inv_Nh, inv_N;    // 1 / Nh, 1 / N (quotient estimates, corrected exactly)
     int mu32;               // nmu^2 * max m < 2^32: mu-bin checks in 32 bits
 };
 

@@ -146,9 +146,6 @@ extern "C" pk_status pk_bin_static(const pk_config *cfg, const void *mesh, const
     bg.koff = (float)(c.kmin / c.dk);
     bg.mlo = static_edge(0, kF, c.kmin, c.dk, mcap);
     bg.mhi = static_edge(nk, kF, c.kmin, c.dk, mcap);
-    bg.modes = (long long)N * N * Nh;
-    bg.inv_Nh = 1.0f / (float)Nh;
-    bg.inv_N = 1.0f / (float)N;
     bg.mu32 = (double)(c.nmu + 1) * (c.nmu + 1) * (double)(bg.mhi + 1) < 4294967295.0 &&
               (double)c.nmu * c.nmu * (double)(N / 2) * (N / 2) < 4294967295.0;
     if (pk::bin_smem_bytes(bg, 0) > 200 * 1024) return static_fail(PK_EINVAL, "histogram too large for shared memory");

@@ -420,7 +420,7 @@ k_survey_ylm(const T *__restrict__ D, const T *__restrict__ Rm, const double *__
 // row of `partial` (the first batch overwrites).  NB > 0: slots [S0, S0 + NB)
 // fixed at compile time; NB = 0: s0, nb.
 template <typename R, typename C, int S0, int NB>
-__global__ void __launch_bounds__(kRowThreads)
+__global__ void __launch_bounds__(kRowThreads, sizeof(R) == 4 ? 6 : 1)
 k_survey_bin(const C *__restrict__ A0, const C *__restrict__ S, long long stride_c, int s0, int nb, int first,
              pk::BinGeom g, const R *__restrict__ cw, const int *__restrict__ kedge, double *__restrict__ partial) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -741,7 +741,7 @@ static pk_status survey_build(pk_survey_s *S, const pk_survey_config *cfg, void 
     SV_CUDA(S, cudaMemset(S->psum, 0, sizeof(double) * 2 * S->G * kSums));
     SV_CUDA(S, cudaMalloc(reinterpret_cast<void **>(&S->cst), sizeof(double) * kConst));
     const int nk = P->bg.nk;
-    S->Gb = S->nsm * 4;
+    S->Gb = S->nsm * 6;                // six 256-thread bin CTAs per SM (registers capped to fit)
     SV_CUDA(S, cudaMalloc(reinterpret_cast<void **>(&S->partial), sizeof(double) * (size_t)S->Gb * 3 * nk));
     SV_CUDA(S, cudaMalloc(reinterpret_cast<void **>(&S->res), sizeof(double) * (3 * (size_t)nk + kConst)));
     SV_CUDA(S, cudaMallocHost(reinterpret_cast<void **>(&S->h_res), sizeof(double) * (3 * (size_t)nk + kConst)));

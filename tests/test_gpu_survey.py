@@ -232,3 +232,17 @@ def test_survey_argument_errors(pk, cats):
         assert e.value.status == pk.PK_ESTATE
     finally:
         pk.pk_survey_destroy(plan)
+
+
+def test_survey_empty_data_and_single_random(pk, cats):
+    """No data objects: alpha = 0 and I = 0, so every P_l is NaN (no crash);
+    a one-object random catalog is accepted."""
+    import torch
+    ext = cats["extent"]
+    cfg = pk.make_survey_config(1.04 * ext, (-0.02 * ext,) * 3, 32)
+    empty = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    gd = pk.survey_catalog(empty)
+    gr, kr = _gpu_cat(pk, torch, cats["randoms"][:1], None, cats["rand_nbar"][:1])
+    got, _ = _run_gpu(pk, cfg, gd, gr)
+    assert got["n_data"] == 0 and got["alpha"] == 0.0 and got["norm"] == 0.0
+    assert np.all(np.isnan(got["poles"][:, got["modes"] > 0]))
