@@ -674,7 +674,7 @@ pk_status pk_compute(pk_plan_t P) {
                                nitems, P->d_res, st));
     if (tm) PK_CUDA(P, cudaEventRecord(P->tev[6], st));
     P->tev_compute = tm;
-    P->launches += 3;   // bin, reduce, finalize
+    P->launches += 2 + reduce_launches(G);   // bin, reduce (one or two passes), finalize
     PK_CUDA(P, cudaMemcpyAsync(P->h_res, P->d_res, sizeof(double) * (size_t)nitems * P->fg.RL,
                                cudaMemcpyDeviceToHost, st));
     // Under stream capture the results come from a later graph replay, which
@@ -716,7 +716,7 @@ pk_status pk_cross(pk_plan_t P, int item_a, int item_b) {
     PK_CUDA(P, launch_bin_reduce(P->d_partial, P->f64, P->G_total, P->bg.nh, 1, P->d_sums2, st));
     PK_CUDA(P, launch_finalize_cross(P->d_sums2, P->G_total, P->d_modes1d, P->d_modes2d, P->d_wsums, P->d_err,
                                      P->fg, item_a, item_b, P->d_xres, st));
-    P->launches += 3;
+    P->launches += 2 + reduce_launches(P->G_total);
     PK_CUDA(P, cudaMemcpyAsync(P->h_xres, P->d_xres, sizeof(double) * (size_t)P->fg.RL, cudaMemcpyDeviceToHost,
                                st));
     const int cap = capturing(st);

@@ -104,6 +104,7 @@ size_t bin_smem_bytes(const BinGeom &g, int f64);
 int bin_ctas_per_sm(const BinGeom &g, int f64);
 int bin_threads();
 int reduce_chunks(int G);
+int reduce_launches(int G);           // k_bin_reduce launches per launch_bin_reduce
 cudaError_t launch_bin_reduce(const void *partial, int f64, int G, int nh, int nitems,
                               double *sums2, cudaStream_t st);
 cudaError_t launch_finalize(const double *sums2, int G, const unsigned long long *modes1d,

@@ -52,7 +52,7 @@ namespace {
 
 constexpr int kCountThreads = 256;
 constexpr int kPaintThreads = 256;
-constexpr int kBinThreads = 512;
+constexpr int kBinThreads = 256;
 constexpr int kBinVec = 4;            // consecutive modes per thread
 constexpr int kScanThreads = 1024;
 constexpr int kScanPer = 4;           // elements per thread in a scan block
@@ -956,7 +956,7 @@ __device__ __forceinline__ int isqrt_floor(int x) {
 // catalog at meshb; each mode contributes Re(delta_a conj(delta_b)) instead
 // of |delta|^2.  MU32: the mu-bin test q^2 m <= nmu^2 l^2 fits in 32 bits.
 template <bool IL, bool TWOD, bool POLES, typename R, typename C, typename A, bool CROSS = false, bool MU32 = true>
-__global__ void __launch_bounds__(kBinThreads, sizeof(R) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(kBinThreads, sizeof(R) == 4 ? 5 : 1)
 k_bin(const C *__restrict__ mesh, long long item_stride_c, long long mesh_stride_c, BinGeom g,
       const R *__restrict__ cw, const C *__restrict__ ph, const int *__restrict__ kedge, A *__restrict__ partial,
       const C *__restrict__ meshb) {
@@ -1106,8 +1106,11 @@ k_bin(const C *__restrict__ mesh, long long item_stride_c, long long mesh_stride
 }
 
 // sums2[(item * nchunk + chunk) * nh + k] = sum of the chunk's per-CTA histograms, in order.
+// out_rows: rows per catalog in sums2 (a second pass over sums2 itself, with
+// G = out_rows, sums each column of a catalog's rows into its row 0 in place:
+// a thread reads and writes only its own column).
 template <typename A>
-__global__ void k_bin_reduce(const A *__restrict__ partial, int G, int nh, int nchunk,
+__global__ void k_bin_reduce(const A *__restrict__ partial, int G, int nh, int out_rows,
                              double *__restrict__ sums2) {
     const int item = blockIdx.z, chunk = blockIdx.y;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1116,14 +1119,14 @@ __global__ void k_bin_reduce(const A *__restrict__ partial, int G, int nh, int n
     const A *p = partial + ((long long)item * G) * nh + k;
     double s = 0.0;
     for (int c = c0; c < c1; ++c) s += (double)p[(long long)c * nh];
-    sums2[((long long)item * nchunk + chunk) * nh + k] = s;
+    sums2[((long long)item * out_rows + chunk) * nh + k] = s;
 }
 
 // Auto power of every catalog (cross_b < 0: block = catalog), or the cross
 // power of catalogs cross_a and cross_b (one block): normalization
 // L^3 / (sum w_a sum w_b), no shot noise; the result block then carries
 // sum w_a and sum w_b in its wsum and w2sum slots.
-__global__ void k_finalize(const double *__restrict__ sums2, int nchunk,
+__global__ void k_finalize(const double *__restrict__ sums2, int nchunk, int nsum,
                            const unsigned long long *__restrict__ modes1d,
                            const unsigned long long *__restrict__ modes2d,
                            const double *__restrict__ wsums, const int *__restrict__ err,
@@ -1142,7 +1145,7 @@ __global__ void k_finalize(const double *__restrict__ sums2, int nchunk,
     const double nan = __longlong_as_double(0x7ff8000000000000LL);
     auto S = [&](int k) {
         double t = 0.0;
-        for (int c = 0; c < nchunk; ++c) t += s0[(long long)c * f.nh + k];
+        for (int c = 0; c < nsum; ++c) t += s0[(long long)c * f.nh + k];
         return t;
     };
     for (int b = threadIdx.x; b < f.nk; b += blockDim.x) {
@@ -1598,13 +1601,19 @@ int bin_ctas_per_sm(const BinGeom &g, int f64) {
 }
 
 int reduce_chunks(int G) { return (G + kReduceChunk - 1) / kReduceChunk; }
+int reduce_launches(int G) { return reduce_chunks(G) > 1 ? 2 : 1; }
 
 cudaError_t launch_bin_reduce(const void *partial, int f64, int G, int nh, int nitems,
                               double *sums2, cudaStream_t st) {
     const int nchunk = reduce_chunks(G);
+    if (nchunk > kReduceChunk) return cudaErrorInvalidValue;    // the second pass is one chunk
     dim3 grid((nh + 127) / 128, nchunk, nitems);
     if (f64) k_bin_reduce<double><<<grid, 128, 0, st>>>(reinterpret_cast<const double *>(partial), G, nh, nchunk, sums2);
     else k_bin_reduce<float><<<grid, 128, 0, st>>>(reinterpret_cast<const float *>(partial), G, nh, nchunk, sums2);
+    if (nchunk > 1) {       // the chunk rows of each catalog into its row 0 (kReduceChunk >= nchunk)
+        dim3 g2((nh + 127) / 128, 1, nitems);
+        k_bin_reduce<double><<<g2, 128, 0, st>>>(sums2, nchunk, nh, nchunk, sums2);
+    }
     return cudaGetLastError();
 }
 
@@ -1612,7 +1621,7 @@ cudaError_t launch_finalize(const double *sums2, int G, const unsigned long long
                             const unsigned long long *modes2d, const double *wsums, const int *err,
                             const FinalGeom &f, int nitems, double *res, cudaStream_t st) {
     const ResultLayout rl = result_layout(f.nk, f.nmu);
-    k_finalize<<<nitems, 256, 0, st>>>(sums2, reduce_chunks(G), modes1d, modes2d, wsums, err, f, rl, res, -1, -1);
+    k_finalize<<<nitems, 256, 0, st>>>(sums2, reduce_chunks(G), 1, modes1d, modes2d, wsums, err, f, rl, res, -1, -1);
     return cudaGetLastError();
 }
 
@@ -1620,7 +1629,7 @@ cudaError_t launch_finalize_cross(const double *sums2, int G, const unsigned lon
                                   const unsigned long long *modes2d, const double *wsums, const int *err,
                                   const FinalGeom &f, int item_a, int item_b, double *res, cudaStream_t st) {
     const ResultLayout rl = result_layout(f.nk, f.nmu);
-    k_finalize<<<1, 256, 0, st>>>(sums2, reduce_chunks(G), modes1d, modes2d, wsums, err, f, rl, res, item_a,
+    k_finalize<<<1, 256, 0, st>>>(sums2, reduce_chunks(G), 1, modes1d, modes2d, wsums, err, f, rl, res, item_a,
                                   item_b);
     return cudaGetLastError();
 }
