@@ -30,6 +30,7 @@ struct pk_plan_s {
     // shared work area.
     std::vector<int> fft_items;
     std::vector<cufftHandle> fft;
+    int fft_single = 0;              // one single-mesh plan, one call per mesh (large meshes)
     void *fft_work = nullptr;
 
     uint32_t *d_count = nullptr;     // objects per (tile, class) key
@@ -75,3 +76,12 @@ struct pk_plan_s {
     long long launches = 0;         // library kernels launched on this plan
     std::string err;
 };
+
+// Meshes with N above this are transformed one per cuFFT call.
+constexpr int kSingleFftAbove = 512;
+
+namespace pk {
+// r2c of `count` consecutive meshes of the plan's layout starting at `first`
+// (batched plans: count must equal the meshes of one catalog).
+cufftResult transform_meshes(pk_plan_s *P, void *first, int count);
+}  // namespace pk

@@ -981,12 +981,7 @@ static pk_status survey_compute_t(pk_survey_s *S) {
         k_fkp_combine<R><<<S->nsm * 8, 256, 0, st>>>(D, Rm, (long long)S->nm * mr, S->cst);
         SV_CUDA(S, cudaGetLastError());
         SV_CUDA(S, tmark(S, 1, PK_SURVEY_STAGE_FFT));
-        if (S->f64) {
-            SV_CUFFT(S, cufftExecD2Z(P->fft[0], reinterpret_cast<cufftDoubleReal *>(D),
-                                     reinterpret_cast<cufftDoubleComplex *>(D)));
-        } else {
-            SV_CUFFT(S, cufftExecR2C(P->fft[0], reinterpret_cast<cufftReal *>(D), reinterpret_cast<cufftComplex *>(D)));
-        }
+        SV_CUFFT(S, pk::transform_meshes(P, D, S->nm));
         C *f1 = reinterpret_cast<C *>(D);
         const R inv_n3 = (R)(1.0 / ((double)N * N * N));
         SV_CUDA(S, tmark(S, 1, PK_SURVEY_STAGE_FIELD));
@@ -1048,15 +1043,7 @@ static pk_status survey_compute_t(pk_survey_s *S) {
             S->launches += 1;
         }
         SV_CUDA(S, tmark(S, 1, PK_SURVEY_STAGE_FFT));
-        if (a0copy) {
-            if (S->f64) {
-                SV_CUFFT(S, cufftExecD2Z(P->fft[0], reinterpret_cast<cufftDoubleReal *>(A0r),
-                                         reinterpret_cast<cufftDoubleComplex *>(A0r)));
-            } else {
-                SV_CUFFT(S, cufftExecR2C(P->fft[0], reinterpret_cast<cufftReal *>(A0r),
-                                         reinterpret_cast<cufftComplex *>(A0r)));
-            }
-        }
+        if (a0copy) SV_CUFFT(S, pk::transform_meshes(P, A0r, 1));
         for (int k = 0; k < nb; ++k) {
             R *mk = SL + (long long)k * mr;
             if (S->f64) {
