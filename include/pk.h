@@ -452,15 +452,17 @@ typedef struct {
 void pk_survey_config_default(pk_survey_config *cfg);
 
 /* Create a survey plan: validates cfg, allocates two catalogs' meshes, the
- * A_0 transform, the Y_lm-weighted meshes of one batch and the cuFFT plans, tabulates chi(z) when omega_m > 0, and computes the mode counts and
- * mean k of the k bins.  All work runs on `cuda_stream`.  Errors: PK_EINVAL
+ * A_0 transform, the Y_lm-weighted meshes of one batch and the cuFFT plans,
+ * tabulates chi(z) when omega_m > 0, and computes the mode counts and mean k
+ * of the k bins.  All work runs on `cuda_stream`.  Errors: PK_EINVAL
  * (message through pk_plan_error), PK_ENOMEM, PK_ECUDA, PK_ECUFFT; on error
  * *out is NULL. */
 pk_status pk_survey_plan(const pk_survey_config *cfg, void *cuda_stream, pk_survey_t *out);
 
 /* Convert (sky input) and paint the data and randoms: each object becomes
- * box-frame (x - box_origin, w) in FP32, the catalog sums of alpha, I and S
- * are taken in FP64, and both catalogs are painted into their own meshes
+ * box-frame (x - box_origin, w) (FP32; FP64 positions for FP64 meshes), the
+ * catalog sums of alpha, I and S are taken in FP64, and both catalogs are
+ * painted into their own meshes
  * (int64 fixed point, as pk_paint).  randoms == NULL keeps the randoms
  * painted by the previous call (mocks that share one random catalog).
  * With no data objects alpha and I are 0 and every P_l is NaN.

@@ -440,7 +440,7 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
         PK_CUDA(P, cudaMemcpy(P->d_modes1d, P->modes1d.data(), 8 * nk, cudaMemcpyHostToDevice));
     }
 
-    // ---- cuFFT: batched in-place r2c, plans over 1, 2, 4, ... catalogs and all B ----
+    // ---- cuFFT: in-place r2c; plans over 1, 2, 4, ... catalogs and all B, or one single-mesh plan ----
     {
         // Meshes above 512^3 are transformed one per call: at 1024^3 a plan
         // batched over two meshes took 18.4 ms against 10.9 ms for two
