@@ -507,6 +507,18 @@ pk_status pk_survey_result(pk_survey_t plan, pk_survey_result_view *out);
  * evaluates on the device, here in FP64 on the host); NaN for other (l, m). */
 double pk_survey_ylm(int l, int m, double x, double y, double z);
 
+/* Bounding box of a catalog's observer-frame Cartesian positions (sky input
+ * converted exactly as pk_survey_paint converts it; sky objects with z
+ * outside [0, zmax] or NaN are skipped), so that the mesh box can be chosen
+ * to enclose the randoms before a survey plan exists.  omega_m and zmax as in
+ * pk_survey_config (used for PK_COORD_SKY only; zmax 0 selects 5).  Runs on
+ * `cuda_stream` and waits for the result; lo / hi receive the minimum and
+ * maximum per axis (+inf / -inf when no object counts).  Host arrays are
+ * copied first.  Errors: PK_EINVAL (NULL cat / lo / hi, dtype, coord, sky
+ * input without omega_m in (0, 1]), PK_ENOMEM, PK_ECUDA. */
+pk_status pk_survey_bounds(const pk_survey_catalog *cat, double omega_m, double zmax, void *cuda_stream,
+                           double *lo, double *hi);
+
 /* Stages whose device time pk_survey_stage_times reports. */
 typedef enum {
     PK_SURVEY_STAGE_PREP = 0,    /* catalog conversion + sums (pk_survey_paint)     */

@@ -30,7 +30,8 @@ __all__ = [
     "pk_paint_many", "pk_compute", "pk_result", "pk_mesh", "pk_destroy", "pk_status_string",
     "pk_last_error", "pk_enable_timing", "pk_stage_times", "pk_launch_count", "FFTPower", "load",
     "build", "make_survey_config", "survey_catalog", "pk_survey_plan", "pk_survey_paint", "pk_survey_compute",
-    "pk_survey_result", "pk_survey_ylm", "pk_survey_destroy", "ConvolvedFFTPower",
+    "pk_survey_result", "pk_survey_ylm", "pk_survey_destroy", "ConvolvedFFTPower", "pk_survey_bounds",
+    "survey_box",
 ]
 
 PK_OK, PK_EINVAL, PK_ENOMEM, PK_ECUDA, PK_ECUFFT, PK_EOVERFLOW, PK_ETIMEOUT, PK_ESTATE = range(8)
@@ -47,7 +48,7 @@ EXPORTED = ["pk_config_default", "pk_plan", "pk_paint", "pk_paint_many", "pk_com
             "pk_lognormal_amp", "pk_lognormal_launch_count", "pk_lognormal_error", "pk_lognormal_destroy",
             "pk_survey_config_default", "pk_survey_plan", "pk_survey_paint", "pk_survey_compute",
             "pk_survey_result", "pk_survey_ylm", "pk_survey_launch_count", "pk_survey_error",
-            "pk_survey_destroy", "pk_survey_enable_timing", "pk_survey_stage_times"]
+            "pk_survey_destroy", "pk_survey_enable_timing", "pk_survey_stage_times", "pk_survey_bounds"]
 STAGES = ["sort", "paint", "fft", "bin", "final"]
 
 
@@ -203,6 +204,9 @@ def load():
         lib.pk_survey_launch_count.restype = ctypes.c_longlong
         lib.pk_survey_error.argtypes = [vp]
         lib.pk_survey_error.restype = ctypes.c_char_p
+        lib.pk_survey_bounds.argtypes = [ctypes.POINTER(pk_survey_catalog), ctypes.c_double, ctypes.c_double, vp,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        lib.pk_survey_bounds.restype = i
         lib.pk_survey_enable_timing.argtypes = [vp, i]
         lib.pk_survey_enable_timing.restype = i
         lib.pk_survey_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
@@ -646,6 +650,27 @@ def pk_survey_result(plan) -> dict:
 
 def pk_survey_ylm(l, m, x, y, z) -> float:
     return float(load().pk_survey_ylm(int(l), int(m), float(x), float(y), float(z)))
+
+
+def pk_survey_bounds(cat: pk_survey_catalog, omega_m=0.31, zmax=5.0, stream=None):
+    """Per-axis (min, max) of a catalog's observer-frame Cartesian positions
+    (sky input converted on the device as the survey paint converts it)."""
+    lo = (ctypes.c_double * 3)()
+    hi = (ctypes.c_double * 3)()
+    status = load().pk_survey_bounds(ctypes.byref(cat), float(omega_m), float(zmax), _stream_ptr(stream), lo, hi)
+    _check(status)
+    return np.array(list(lo)), np.array(list(hi))
+
+
+def survey_box(lo, hi, pad=0.02):
+    """Cubic mesh box enclosing [lo, hi]: edge (1 + pad) times the largest
+    extent, centred on the middle of the range.  Returns (box_size, origin)."""
+    lo, hi = np.asarray(lo, dtype=np.float64), np.asarray(hi, dtype=np.float64)
+    size = float(np.max(hi - lo)) * (1.0 + float(pad))
+    if not size > 0.0:
+        raise ValueError("empty or degenerate range")
+    origin = 0.5 * (lo + hi) - 0.5 * size
+    return size, tuple(float(v) for v in origin)
 
 
 SURVEY_STAGES = ["prep", "paint", "fft", "field", "bin", "final"]

@@ -137,6 +137,82 @@ struct PrepArgs {
     double dz, inv_dz, zmax;
 };
 
+// Observer-frame position of object i: Cartesian input as given; sky input
+// (RA, Dec in degrees, z) through chi(z).  False (and the box origin) for a
+// sky object with z outside [0, zmax] or NaN.
+template <typename P, bool SKY>
+__device__ __forceinline__ bool observer_xyz(const P *__restrict__ pos, long long i, const PrepArgs &a, double *x,
+                                             double *y, double *z) {
+    const double c0 = (double)pos[3 * i], c1 = (double)pos[3 * i + 1], c2 = (double)pos[3 * i + 2];
+    if (!SKY) {
+        *x = c0;
+        *y = c1;
+        *z = c2;
+        return true;
+    }
+    if (!(c2 >= 0.0 && c2 <= a.zmax)) {
+        *x = a.ox;
+        *y = a.oy;
+        *z = a.oz;
+        return false;
+    }
+    const double r = chi_of_z(a.chi, a.nchi, a.inv_dz, a.dz, c2);
+    double sr, cr, sd, cd;
+    sincospi(c0 / 180.0, &sr, &cr);
+    sincospi(c1 / 180.0, &sd, &cd);
+    *x = r * cd * cr;
+    *y = r * cd * sr;
+    *z = r * sd;
+    return true;
+}
+
+// Per-CTA minimum and maximum of the observer-frame positions that count
+// (partial[6 b + {0,1,2}] = min x, y, z; + {3,4,5} = max).
+template <typename P, bool SKY>
+__global__ void __launch_bounds__(kPrepThreads)
+k_survey_bounds(const P *__restrict__ pos, long long n, PrepArgs a, double *__restrict__ partial) {
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    double v[6] = {inf, inf, inf, -inf, -inf, -inf};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        double x, y, z;
+        if (!observer_xyz<P, SKY>(pos, i, a, &x, &y, &z)) continue;
+        v[0] = fmin(v[0], x);
+        v[1] = fmin(v[1], y);
+        v[2] = fmin(v[2], z);
+        v[3] = fmax(v[3], x);
+        v[4] = fmax(v[4], y);
+        v[5] = fmax(v[5], z);
+    }
+    __shared__ double red[kPrepThreads / 32][6];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        double t = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double u = __shfl_down_sync(0xffffffffu, t, o);
+            t = k < 3 ? fmin(t, u) : fmax(t, u);
+        }
+        if (lane == 0) red[warp][k] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int k = threadIdx.x;
+        double t = red[0][k];
+        for (int w = 1; w < kPrepThreads / 32; ++w) t = k < 3 ? fmin(t, red[w][k]) : fmax(t, red[w][k]);
+        partial[6LL * blockIdx.x + k] = t;
+    }
+}
+
+__global__ void k_survey_bounds_final(const double *__restrict__ partial, int G, double *__restrict__ out) {
+    const int k = threadIdx.x;
+    if (k >= 6) return;
+    double t = partial[k];
+    for (int b = 1; b < G; ++b) t = k < 3 ? fmin(t, partial[6LL * b + k]) : fmax(t, partial[6LL * b + k]);
+    out[k] = t;
+}
+
 // One catalog -> box-frame positions + weights, and its FP64 sums.
 // F64OUT: positions as double xyz (FP64 meshes) and weights in wout;
 // otherwise float4 xyzw in out4.
@@ -149,32 +225,11 @@ k_survey_prep(const P *__restrict__ pos, long long n, const float *__restrict__ 
     double s_wc = 0.0, s_w2 = 0.0, s_n = 0.0, s_out = 0.0, s_rej = 0.0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const double c0 = (double)pos[3 * i], c1 = (double)pos[3 * i + 1], c2 = (double)pos[3 * i + 2];
         double wc = wcomp ? (double)wcomp[i] : 1.0;
         const double nb = nbar ? (double)nbar[i] : 0.0;
         double wf = a.p0 > 0.0 ? 1.0 / (1.0 + nb * a.p0) : (wfkp ? (double)wfkp[i] : 1.0);
         double x, y, z;
-        bool ok = true;
-        if (SKY) {
-            if (!(c2 >= 0.0 && c2 <= a.zmax)) {
-                ok = false;
-                x = a.ox;
-                y = a.oy;
-                z = a.oz;
-            } else {
-                const double r = chi_of_z(a.chi, a.nchi, a.inv_dz, a.dz, c2);
-                double sr, cr, sd, cd;
-                sincospi(c0 / 180.0, &sr, &cr);
-                sincospi(c1 / 180.0, &sd, &cd);
-                x = r * cd * cr;
-                y = r * cd * sr;
-                z = r * sd;
-            }
-        } else {
-            x = c0;
-            y = c1;
-            z = c2;
-        }
+        const bool ok = observer_xyz<P, SKY>(pos, i, a, &x, &y, &z);
         if (!ok) {
             wc = 0.0;
             wf = 0.0;
@@ -1121,6 +1176,83 @@ pk_status pk_survey_result(pk_survey_t S, pk_survey_result_view *out) {
     out->n_randoms = S->nr;
     out->n_outside = (int64_t)llround(c[9] + c[10]);
     out->n_rejected = (int64_t)llround(c[11] + c[12]);
+    return PK_OK;
+}
+
+pk_status pk_survey_bounds(const pk_survey_catalog *cat, double omega_m, double zmax, void *cuda_stream,
+                           double *lo, double *hi) {
+    if (!cat || !lo || !hi) return sfail(nullptr, PK_EINVAL, "cat, lo and hi must not be NULL");
+    if (cat->dtype != PK_F32 && cat->dtype != PK_F64)
+        return sfail(nullptr, PK_EINVAL, "catalog dtype must be PK_F32 or PK_F64");
+    if (cat->coord != PK_COORD_CARTESIAN && cat->coord != PK_COORD_SKY)
+        return sfail(nullptr, PK_EINVAL, "catalog coord must be PK_COORD_CARTESIAN or PK_COORD_SKY");
+    const bool sky = cat->coord == PK_COORD_SKY;
+    if (sky && !(omega_m > 0.0 && omega_m <= 1.0))
+        return sfail(nullptr, PK_EINVAL, "sky input needs omega_m in (0, 1]");
+    if (!(zmax >= 0.0 && zmax <= 1100.0)) return sfail(nullptr, PK_EINVAL, "zmax must be in [0, 1100]");
+    if (cat->n < 0 || (cat->n > 0 && !cat->pos)) return sfail(nullptr, PK_EINVAL, "catalog pos / n invalid");
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = INFINITY;
+        hi[k] = -INFINITY;
+    }
+    if (cat->n == 0) return PK_OK;
+    const cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    const size_t pbytes = (size_t)cat->n * (cat->dtype == PK_F64 ? 24 : 12);
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return sfail(nullptr, PK_ECUDA, "no CUDA device");
+    }
+    const int G = nsm * kPrepCtasPerSm;
+    std::vector<double> tab;
+    PrepArgs a{};
+    a.nchi = kChiNodes;
+    a.zmax = zmax > 0.0 ? zmax : 5.0;
+    if (sky) chi_table(omega_m, a.zmax, tab, &a.dz);
+    a.inv_dz = a.dz > 0.0 ? 1.0 / a.dz : 0.0;
+    const bool pdev = dev_ptr(cat->pos);
+    // one device block: 6 results | G x 6 per-CTA partials | chi table | positions (host input)
+    const size_t off_part = 64, off_tab = off_part + 48 * (size_t)G;
+    const size_t off_pos = (off_tab + 8 * tab.size() + 255) / 256 * 256;
+    char *buf = nullptr;
+    if (cudaMalloc(reinterpret_cast<void **>(&buf), off_pos + (pdev ? 0 : pbytes)) != cudaSuccess) {
+        cudaGetLastError();
+        return sfail(nullptr, PK_ENOMEM, "device allocation failed");
+    }
+    double *res = reinterpret_cast<double *>(buf);
+    double *part = reinterpret_cast<double *>(buf + off_part);
+    a.chi = sky ? reinterpret_cast<const double2 *>(buf + off_tab) : nullptr;
+    const void *pos = pdev ? cat->pos : buf + off_pos;
+    cudaError_t e = cudaSuccess;
+    if (sky) e = cudaMemcpyAsync(buf + off_tab, tab.data(), 8 * tab.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !pdev) e = cudaMemcpyAsync(buf + off_pos, cat->pos, pbytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        const long long n = cat->n;
+        if (cat->dtype == PK_F64) {
+            const double *pp = reinterpret_cast<const double *>(pos);
+            if (sky) k_survey_bounds<double, true><<<G, kPrepThreads, 0, st>>>(pp, n, a, part);
+            else k_survey_bounds<double, false><<<G, kPrepThreads, 0, st>>>(pp, n, a, part);
+        } else {
+            const float *pp = reinterpret_cast<const float *>(pos);
+            if (sky) k_survey_bounds<float, true><<<G, kPrepThreads, 0, st>>>(pp, n, a, part);
+            else k_survey_bounds<float, false><<<G, kPrepThreads, 0, st>>>(pp, n, a, part);
+        }
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        k_survey_bounds_final<<<1, 32, 0, st>>>(part, G, res);
+        e = cudaGetLastError();
+    }
+    double out[6];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, sizeof(out), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (e != cudaSuccess) return sfail(nullptr, PK_ECUDA, std::string("survey bounds: ") + cudaGetErrorString(e));
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = out[k];
+        hi[k] = out[3 + k];
+    }
     return PK_OK;
 }
 

@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -171,3 +172,23 @@ def test_plan_rejects_too_fine_binning(pk):
     h = ctypes.c_void_p()
     assert pk.load().pk_plan(ctypes.byref(c), None, ctypes.byref(h)) == pk.PK_EINVAL
     assert "too fine" in pk.load().pk_plan_error().decode()
+
+
+def test_survey_bounds_argument_errors(pk):
+    lib = pk.load()
+    lo, hi = (ctypes.c_double * 3)(), (ctypes.c_double * 3)()
+    assert lib.pk_survey_bounds(None, 0.31, 5.0, None, lo, hi) == pk.PK_EINVAL
+    cat = pk.pk_survey_catalog(None, pk.PK_F32, pk.PK_COORD_SKY, None, None, None, 10)
+    assert lib.pk_survey_bounds(ctypes.byref(cat), 0.31, 5.0, None, lo, hi) == pk.PK_EINVAL    # NULL pos
+    cat = pk.pk_survey_catalog(None, pk.PK_F32, pk.PK_COORD_SKY, None, None, None, 0)
+    assert lib.pk_survey_bounds(ctypes.byref(cat), 0.0, 5.0, None, lo, hi) == pk.PK_EINVAL     # no omega_m
+    assert lib.pk_survey_bounds(ctypes.byref(cat), 0.31, 5.0, None, lo, hi) == pk.PK_OK        # empty: no GPU call
+    assert list(lo) == [float("inf")] * 3 and list(hi) == [float("-inf")] * 3
+
+
+def test_survey_box_encloses_the_range(pk):
+    size, origin = pk.survey_box([0.0, -10.0, 5.0], [100.0, 30.0, 45.0], pad=0.1)
+    assert abs(size - 110.0) < 1e-12
+    assert np.allclose(origin, [50.0 - 55.0, 10.0 - 55.0, 25.0 - 55.0])
+    with pytest.raises(ValueError):
+        pk.survey_box([1.0, 1.0, 1.0], [1.0, 1.0, 1.0])

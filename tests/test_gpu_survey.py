@@ -246,3 +246,30 @@ def test_survey_empty_data_and_single_random(pk, cats):
     got, _ = _run_gpu(pk, cfg, gd, gr)
     assert got["n_data"] == 0 and got["alpha"] == 0.0 and got["norm"] == 0.0
     assert np.all(np.isnan(got["poles"][:, got["modes"] > 0]))
+
+
+@pytest.mark.parametrize("device", [True, False])
+def test_survey_bounds_match_the_oracle(pk, sv, device):
+    """Device bounds of sky (RA, Dec, z) and Cartesian catalogs against the
+    oracle's conversion; rejected redshifts are skipped."""
+    import torch
+    import synth
+    om = 0.31
+    d = synth.survey_sky(50000, 43)
+    d["z"][:3] = [-0.5, 7.0, np.nan]
+    keep = np.isfinite(d["z"]) & (d["z"] >= 0) & (d["z"] <= 5.0)
+    x = sv.sky_to_cartesian(d["ra"][keep], d["dec"][keep], d["z"][keep], om)
+    sky = np.stack([d["ra"], d["dec"], d["z"]], axis=1)
+    cat, k = _gpu_cat(pk, torch, sky, coord="sky", device=device)
+    lo, hi = pk.pk_survey_bounds(cat, omega_m=om)
+    scale = float(np.max(np.abs(x)))
+    assert np.all(np.abs(lo - x.min(0)) <= 1e-9 * scale) and np.all(np.abs(hi - x.max(0)) <= 1e-9 * scale)
+    cat2, k2 = _gpu_cat(pk, torch, x, device=device)
+    lo2, hi2 = pk.pk_survey_bounds(cat2)
+    assert np.array_equal(lo2, x.min(0)) and np.array_equal(hi2, x.max(0))
+    L, origin = pk.survey_box(lo, hi, pad=0.02)
+    cfg = pk.make_survey_config(L, origin, 32, omega_m=om)
+    rcat, kr = _gpu_cat(pk, torch, sky[keep][:2000], None, d["nbar"][keep][:2000], coord="sky", device=device)
+    dcat, kd = _gpu_cat(pk, torch, sky, None, None, coord="sky", device=device)
+    got, _ = _run_gpu(pk, cfg, dcat, rcat)
+    assert got["n_outside"] == 0 and got["n_rejected"] == 3
