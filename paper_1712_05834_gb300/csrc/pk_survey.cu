@@ -19,6 +19,8 @@
 //            h cw Y_lm(k^) Re[A_lm A_0^*] (and h cw |A_0|^2 once) into
 //            per-CTA FP64 rows; k_survey_final reduces the rows in a fixed
 //            order and normalizes.
+//   bounds   k_survey_bounds + k_survey_bounds_final: a catalog's observer-
+//            frame bounding box (pk_survey_bounds), for choosing the box.
 #include <cuda_runtime.h>
 #include <cufft.h>
 
