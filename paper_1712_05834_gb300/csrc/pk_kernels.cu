@@ -457,6 +457,9 @@ __device__ __forceinline__ void deposit_flat(unsigned *sm, int cell0, unsigned t
     }
 #pragma unroll
     for (int a = 0; a < P; ++a) {
+        // TSC: skip an x plane that lies wholly outside the tile (measured
+        // faster for TSC, slower for PCS, whose lanes diverge more)
+        if (P == 3 && ox[a] == kOut) continue;
         const float vxw = ws * wx[a];
 #pragma unroll
         for (int b = 0; b < P; ++b) {
