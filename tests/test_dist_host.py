@@ -61,3 +61,20 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
         steps, warmup = 1, 0
     assert bench.run_reference(Args()) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_binned_stored_modes_counts_the_modes_in_k_bins():
+    """The bench's algorithmic-bytes helper counts stored half-grid modes with
+    0 < |k| and a k bin in [0, nk): checked by direct enumeration."""
+    import math
+    import numpy as np
+    import bench
+    N, L, dk = 48, 300.0, 0.03
+    kF = 2 * math.pi / L
+    nk = int(math.floor((math.pi * N / L) / dk))
+    f = np.fft.fftfreq(N, 1.0 / N)
+    I, J, K = np.meshgrid(f, f, np.arange(N // 2 + 1), indexing="ij")
+    m = I * I + J * J + K * K
+    b = np.floor(kF * np.sqrt(m) / dk)
+    want = int(np.count_nonzero((m > 0) & (b >= 0) & (b < nk)))
+    assert bench.binned_stored_modes(N, L, dk) == want

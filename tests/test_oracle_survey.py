@@ -149,3 +149,17 @@ def test_poisson_survey_gives_fkp_shot_noise(sv, window, interlaced):
 def test_planted_shot_noise_without_randoms_term_is_rejected(sv):
     chi2, dof, zmax, pval = _poisson_survey_chi2(sv, "cic", False, seeds=[301, 302, 303], drop_alpha2=True)
     assert pval < 1e-6, (chi2, dof, pval)
+
+
+def test_planted_global_line_of_sight_is_rejected(sv):
+    """Negative control for the per-node pin: multipoles about a fixed z axis
+    (an observer far away) differ from the local-line-of-sight definition for
+    an observer near the box, far beyond rounding."""
+    N, L, near = 8, 80.0, (-40.0, -35.0, -30.0)
+    rng = np.random.default_rng(5)
+    F = rng.normal(size=(N, N, N))
+    truth = sv.multipoles_direct(F, L, near)
+    planted = sv.multipole_fields(F, L, (-0.5 * L, -0.5 * L, 1e12))
+    scale = np.max(np.abs(truth[0]))
+    assert np.max(np.abs(planted[2] - truth[2])) > 1e-2 * scale
+    assert np.max(np.abs(planted[4] - truth[4])) > 1e-2 * scale
