@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--no-study", action="store_true", help="skip the window / interlacing accuracy study")
     ap.add_argument("--no-survey", action="store_true", help="skip the survey-multipole measurement")
+    ap.add_argument("--no-windows", action="store_true", help="skip the paint time per window")
     ap.add_argument("--profile", action="store_true",
                     help="timed steps only (no e2e leg, no CPU baseline, no clock sampler): for ncu")
     return ap.parse_args()
@@ -528,6 +529,36 @@ def measure_window_study(torch, rank):
             "wall_s": wall}
 
 
+def measure_window_speed(pk, torch, stream, pos, reps=10, warmup=3):
+    """Paint time (sort + tile paint) of the main catalog for each window,
+    with and without interlacing, beside the paper's relative paint speeds
+    (TSC about 10 %, PCS about 40 % slower than CIC, Sec. 3.3.2)."""
+    out = {}
+    try:
+        for window in ("cic", "tsc", "pcs"):
+            for il in (False, True):
+                plan = pk.pk_plan(pk.make_config(L_BOX, NMESH, window, interlaced=il, dk=DK), stream)
+                try:
+                    pk.pk_enable_timing(plan, True)
+                    ts = []
+                    for k in range(warmup + reps):
+                        pk.pk_paint(plan, pos)
+                        pk.pk_compute(plan)
+                        pk.pk_result(plan, 0)
+                        st = pk.pk_stage_times(plan)
+                        if k >= warmup:
+                            ts.append(st["sort"] + st["paint"])
+                finally:
+                    pk.pk_destroy(plan)
+                out[window + ("+interlacing" if il else "")] = statistics.median(ts)
+    except Exception as e:             # a side measurement never costs the main line
+        return {"error": repr(e)}
+    base = out["cic"]
+    return {"workload": "the main catalog (1e7 log-normal objects) on 512^3, sort + tile paint, median of %d"
+                        % reps,
+            "ms": out, "ratio_to_cic": {k: v / base for k, v in out.items()}}
+
+
 def measure_survey(pk, torch, stream, world, rank, steps=5, warmup=2):
     """Survey multipoles (ConvolvedFFTPower) on the paper's "small" benchmark
     sample: 1e6 galaxies in a 2500 Mpc/h survey volume, Nmesh 1024, l = 0, 2,
@@ -702,6 +733,7 @@ def main():
         pk.pk_destroy(plan)
         del flush
         torch.cuda.empty_cache()
+        windows = None if (args.no_windows or args.profile) else measure_window_speed(pk, torch, stream, pos)
         big = None if (args.no_2048 or args.profile) else measure_2048(pk, torch, stream, world)
         batched = None if (args.no_batched or args.profile) else measure_batched(pk, torch, world, rank)
         served = None if (args.no_serve or args.profile) else measure_serving(pk, torch, world, rank,
@@ -773,6 +805,8 @@ def main():
         line["window_study"] = study
     if survey is not None:
         line["survey_multipoles"] = survey
+    if windows is not None:
+        line["paint_by_window"] = windows
     if world == 1 and not args.no_cpu_baseline and not args.profile:
         import oracle
         oracle.build()
