@@ -17,10 +17,12 @@
 //                   (the split point is chosen per tile so the low word can
 //                   never carry; shared 32-bit atomics are ~5x faster than
 //                   64-bit ones here), then write the tile once, coalesced,
-//                   into the in-place r2c layout.  One mesh per pass; the
-//                   interlaced mesh is a second pass over the same objects.
-//                   Integer adds are order-free: the mesh is bit-identical
-//                   run to run and for any object order.
+//                   into the in-place r2c layout.  Unit weights: one sweep
+//                   over the candidates deposits both interlaced meshes (one
+//                   32-bit word per cell each), branch-free in sparse tiles;
+//                   weighted objects: one mesh per pass over staged
+//                   candidates.  Integer adds are order-free: the mesh is
+//                   bit-identical run to run and for any object order.
 //   k_paint_atomic  the variant without a sort: one thread per object adds
 //                   each deposit with a 64-bit global atomic into a dense
 //                   int64 accumulator per mesh (as order-free as the tiles);
@@ -28,12 +30,14 @@
 //                   them.  Cheaper than sorting for small meshes that stay in
 //                   L2; the plan's paint_variant picks one of the two.
 // Bin (Sec. 3.4.1, Eq. window-deconvolution):
-//   k_bin           per stored mode: interlace combine, sinc^p compensation,
-//                   |delta|^2, k bin (exact integer edges in m = |n|^2), mu
-//                   bin (exact integer rule), Legendre mu^2 / mu^4 weights;
-//                   runs of equal bins merged in registers, then per-CTA
-//                   shared-memory histograms.
-//   k_bin_reduce    fixed-order FP64 sums of the per-CTA histograms, in chunks.
+//   k_bin           warps take whole rows of the stored half grid and visit
+//                   only the binned l range; per mode: interlace combine,
+//                   sinc^p compensation, |delta|^2, k bin (exact integer
+//                   edges in m = |n|^2), mu bin (exact integer rule),
+//                   Legendre mu^2 / mu^4 weights; runs of equal bins merged
+//                   in registers, then per-CTA shared-memory histograms.
+//   k_bin_reduce    fixed-order FP64 sums of the per-CTA histograms in 32-row
+//                   chunks, then (in place) of the chunks.
 //   k_finalize      normalization L^3 / (sum w)^2, shot noise, multipoles.
 // Plan time (geometry only):
 //   k_geom_*        exact mode counts per bin and mean k, mean mu from integer
