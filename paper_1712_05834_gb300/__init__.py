@@ -9,6 +9,18 @@ this module only marshals arguments to the C ABI declared in
 ``include/pk.h`` and keeps its names: ``pk_plan``, ``pk_paint``,
 ``pk_paint_many``, ``pk_compute``, ``pk_result``, ``pk_mesh``, ``pk_destroy``.
 
+The survey multipoles of ConvolvedFFTPower (Sec. 3.4.1) use the same library
+through ``pk_survey_plan``, ``pk_survey_paint``, ``pk_survey_compute``,
+``pk_survey_result`` (and ``pk_survey_bounds`` / ``survey_box`` to choose the
+mesh box), e.g.::
+
+    lo, hi = pk_survey_bounds(survey_catalog(randoms_radecz, "sky", nbar=nz_r))
+    L, origin = survey_box(lo, hi, pad=0.02)
+    with ConvolvedFFTPower(make_survey_config(L, origin, 512, "tsc", True)) as cp:
+        res = cp.run(survey_catalog(data_radecz, "sky", wcomp=wc, nbar=nz_d),
+                     survey_catalog(randoms_radecz, "sky", nbar=nz_r))
+    res["poles"]      # P_0, P_2, P_4 per k bin
+
 There is no fallback: if the library is missing or no GPU is present the calls
 raise.  ``build()`` compiles the library in-tree (nvcc, sm_103a).
 """
