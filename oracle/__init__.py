@@ -5,9 +5,9 @@ TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and
 this package.  It shares no code with the CUDA library and never imports it.
 
 The arithmetic lives in ``pk_oracle.c`` (plain FP64 loops, one function per
-step of the method).  This module only marshals arrays, calls numpy's FFT as
-the library primitive between painting and binning (Sec. 3.3.1: the real and
-complex fields are related by an r2c FFT), and finalizes the bin sums:
+step of the method, including its own mixed-radix FFT between painting and
+binning: Sec. 3.3.1 relates the real and complex fields by an r2c FFT).  This
+module only marshals arrays and finalizes the bin sums:
 
     P(k, mu) = sum h P / sum h - P_shot                      (Sec. 3.4.1)
     P_l(k)   = (2l + 1) sum h P L_l(mu) / sum h - [l = 0] P_shot
@@ -67,6 +67,12 @@ def _load():
         lib.oracle_paint_block.restype = i
         lib.oracle_mode_counts.argtypes = [i, d, d, d, i, i, p, p]
         lib.oracle_mode_counts.restype = i
+        lib.oracle_r2c.argtypes = [p, i, p]
+        lib.oracle_r2c.restype = i
+        lib.oracle_twiddles.argtypes = [i, p]
+        lib.oracle_twiddles.restype = None
+        lib.oracle_dft_line.argtypes = [p, i, p, p]
+        lib.oracle_dft_line.restype = None
         lib.oracle_philox4x64.argtypes = [p, p, p]
         lib.oracle_philox4x64.restype = None
         lib.oracle_white_noise.argtypes = [i, ctypes.c_uint64, p]
@@ -138,8 +144,28 @@ def mode_counts(nmesh, box_size, dk, kmin=0.0, kmax=None, nmu=0):
 
 
 def r2c(mesh):
-    """Forward r2c transform, F~(n) = sum_c F[c] exp(-2 pi i c.n / N), last axis halved."""
-    return np.fft.rfftn(mesh)
+    """Forward r2c transform, F~(n) = sum_c F[c] exp(-2 pi i c.n / N), last axis
+    halved: the oracle's own mixed-radix FFT (pk_oracle.c, oracle_r2c)."""
+    mesh = np.ascontiguousarray(mesh, dtype=np.float64)
+    N = mesh.shape[0]
+    assert mesh.shape == (N, N, N)
+    out = np.empty((N, N, N // 2 + 1), dtype=np.complex128)
+    rc = _load().oracle_r2c(_ptr(mesh), int(N), _ptr(out))
+    if rc != 0:
+        raise MemoryError("oracle_r2c failed (%d)" % rc)
+    return out
+
+
+def dft(x):
+    """One-dimensional transform X[k] = sum_j x[j] exp(-2 pi i j k / n) of a
+    complex vector by the same mixed-radix routine (for its pins)."""
+    x = np.array(x, dtype=np.complex128).reshape(-1)
+    n = x.shape[0]
+    tw = np.empty(2 * n)
+    work = np.empty(4 * n)
+    _load().oracle_twiddles(int(n), _ptr(tw))
+    _load().oracle_dft_line(_ptr(x), int(n), _ptr(tw), _ptr(work))
+    return x
 
 
 def nbins(box_size: float, nmesh: int, dk: float, kmin: float = 0.0, kmax=None) -> int:

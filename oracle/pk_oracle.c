@@ -32,9 +32,17 @@
  *                         P = L^3 Re(delta_a conj(delta_b)) (the cross-correlation
  *                         of two painted fields, e.g. two tracers or a density
  *                         and a momentum field, Sec. 3.3.1).
+ *   oracle_r2c            the forward transform between painting and binning
+ *                         (Sec. 3.3.1: the real field and its complex Fourier
+ *                         field), F~(n) = sum_c F[c] exp(-2 pi i c.n / N), as
+ *                         three passes of a plain mixed-radix Cooley-Tukey FFT
+ *                         (decimation in time by the smallest prime factor; a
+ *                         prime length is summed directly), last axis halved.
  *
- * The FFT between paint and bin is a library primitive (numpy's pocketfft),
- * called from the Python glue in oracle/__init__.py.
+ * Parallel loops (OpenMP) never change a result with the thread count: the
+ * paint gives each thread a fixed range of x planes and adds every object's
+ * deposits in object order; the mode loop sums fixed blocks of x rows and
+ * adds the blocks in order; the FFT works on independent lines.
  *
  * Conventions the paper leaves open (each one also used by the CUDA path and
  * listed with its reasoning in the design notes):
@@ -102,34 +110,60 @@ static int64_t mod_n(int64_t c, int64_t n)
  *   F[c] += w_q * prod_a W_p(s_a - c_a)
  * for every node c within the window support, with s = wrap(x) N / L + shift.
  * pos is n x 3 FP64, w is n FP64 or NULL (unit weights).  The mesh is not
- * cleared.  Returns 0, or -1 on bad arguments. */
+ * cleared.  Each OpenMP thread owns a fixed range of x planes and walks all
+ * objects in order, adding only the deposits that land in its planes, so every
+ * cell receives its deposits in object order whatever the thread count.
+ * Returns 0, or -1 on bad arguments. */
 int oracle_paint(const double *pos, const double *w, int64_t n, double L, int N,
                  int p, double shift, double *mesh)
 {
     if (N < 1 || L <= 0.0 || (p < 2 || p > 4)) return -1;
     const int64_t NN = (int64_t)N;
-    for (int64_t q = 0; q < n; ++q) {
-        double wa[3][8];
-        int64_t ia[3][8];
-        for (int a = 0; a < 3; ++a) {
-            double x = pos[3 * q + a];
-            x = x - L * floor(x / L);              /* periodic wrap into [0, L) */
-            double s = x * (double)N / L + shift;  /* cell units */
-            int64_t c0 = (int64_t)floor(s - 0.5 * p);
-            for (int k = 0; k < p + 2; ++k) {      /* every node within p/2 */
-                int64_t c = c0 + k;
-                wa[a][k] = oracle_window_weight(p, s - (double)c);
-                ia[a][k] = mod_n(c, NN);
+#pragma omp parallel
+    {
+        int nt = 1, t = 0;
+#ifdef _OPENMP
+        nt = omp_get_num_threads();
+        t = omp_get_thread_num();
+#endif
+        const int64_t x0 = NN * t / nt, x1 = NN * (t + 1) / nt;   /* this thread's x planes */
+        for (int64_t q = 0; q < n && x0 < x1; ++q) {
+            double wa[3][8];
+            int64_t ia[3][8];
+            int mine = 0;
+            if (NN >= 2 * (p + 2)) {
+                /* skip at once an object whose nodes c0 .. c0 + p + 1 along x
+                 * (periodic) miss the planes [x0, x1) */
+                double x = pos[3 * q];
+                x = x - L * floor(x / L);
+                const int64_t d = mod_n((int64_t)floor(x * (double)N / L + shift - 0.5 * p) - x0, NN);
+                if (d >= x1 - x0 && d + p + 1 < NN) continue;
+            }
+            for (int a = 0; a < 3; ++a) {
+                double x = pos[3 * q + a];
+                x = x - L * floor(x / L);              /* periodic wrap into [0, L) */
+                double s = x * (double)N / L + shift;  /* cell units */
+                int64_t c0 = (int64_t)floor(s - 0.5 * p);
+                for (int k = 0; k < p + 2; ++k) {      /* every node within p/2 */
+                    int64_t c = c0 + k;
+                    wa[a][k] = oracle_window_weight(p, s - (double)c);
+                    ia[a][k] = mod_n(c, NN);
+                    if (a == 0 && ia[0][k] >= x0 && ia[0][k] < x1) mine = 1;
+                }
+                if (a == 0 && !mine) break;            /* no deposit in this thread's planes */
+            }
+            if (!mine) continue;
+            double wq = w ? w[q] : 1.0;
+            for (int kx = 0; kx < p + 2; ++kx) {
+                if (ia[0][kx] < x0 || ia[0][kx] >= x1) continue;
+                for (int ky = 0; ky < p + 2; ++ky)
+                    for (int kz = 0; kz < p + 2; ++kz) {
+                        double v = wq * wa[0][kx] * wa[1][ky] * wa[2][kz];
+                        if (v == 0.0) continue;
+                        mesh[(ia[0][kx] * NN + ia[1][ky]) * NN + ia[2][kz]] += v;
+                    }
             }
         }
-        double wq = w ? w[q] : 1.0;
-        for (int kx = 0; kx < p + 2; ++kx)
-            for (int ky = 0; ky < p + 2; ++ky)
-                for (int kz = 0; kz < p + 2; ++kz) {
-                    double v = wq * wa[0][kx] * wa[1][ky] * wa[2][kz];
-                    if (v == 0.0) continue;
-                    mesh[(ia[0][kx] * NN + ia[1][ky]) * NN + ia[2][kz]] += v;
-                }
     }
     return 0;
 }
@@ -290,21 +324,17 @@ static void mode_delta(const double *F1, const double *F2, int64_t idx, int64_t 
     *im_out = im / wsum;
 }
 
-/* The same loop for the cross power of two catalogs painted on equal meshes:
- * P = L^3 Re(delta_a conj(delta_b)) with each delta formed as above from its
- * own transforms (G1, G2) and total weight (wsum_b).  G1 = NULL gives the
- * auto power of the first catalog. */
-int oracle_bin_pair(const double *F1, const double *F2, const double *G1, const double *G2, int N,
-                    double L, int p, int compensated, double wsum, double wsum_b, double kmin, double dk,
-                    int nk, int nmu, int64_t *modes1d, double *ksum1d, double *psum1d, double *p2sum1d,
-                    double *p4sum1d, int64_t *modes2d, double *ksum2d, double *musum2d, double *psum2d)
+/* The mode loop over the x rows i0 <= i < i1, adding into the given sums. */
+static void bin_rows(const double *F1, const double *F2, const double *G1, const double *G2, int N,
+                     double L, int p, int compensated, double wsum, double wsum_b, double kmin, double dk,
+                     int nk, int nmu, int64_t i0, int64_t i1, int64_t *modes1d, double *ksum1d, double *psum1d,
+                     double *p2sum1d, double *p4sum1d, int64_t *modes2d, double *ksum2d, double *musum2d,
+                     double *psum2d)
 {
-    if (N < 2 || (N % 2) != 0 || L <= 0.0 || dk <= 0.0 || nk < 0 || nmu < 0)
-        return -1;
     const int64_t NN = N, Nh = N / 2 + 1;
     const double kF = (2.0 * M_PI) / L;
     const double L3 = L * L * L;
-    for (int64_t i = 0; i < NN; ++i) {
+    for (int64_t i = i0; i < i1; ++i) {
         int64_t ip = i < NN / 2 ? i : i - NN;       /* fftfreq */
         for (int64_t j = 0; j < NN; ++j) {
             int64_t jp = j < NN / 2 ? j : j - NN;
@@ -346,6 +376,61 @@ int oracle_bin_pair(const double *F1, const double *F2, const double *G1, const 
             }
         }
     }
+}
+
+/* The same loop for the cross power of two catalogs painted on equal meshes:
+ * P = L^3 Re(delta_a conj(delta_b)) with each delta formed as above from its
+ * own transforms (G1, G2) and total weight (wsum_b).  G1 = NULL gives the
+ * auto power of the first catalog.  The x rows are cut into at most 64 fixed
+ * blocks, each summed on its own (in parallel), and the blocks are added into
+ * the outputs in row order, so the sums do not depend on the thread count. */
+int oracle_bin_pair(const double *F1, const double *F2, const double *G1, const double *G2, int N,
+                    double L, int p, int compensated, double wsum, double wsum_b, double kmin, double dk,
+                    int nk, int nmu, int64_t *modes1d, double *ksum1d, double *psum1d, double *p2sum1d,
+                    double *p4sum1d, int64_t *modes2d, double *ksum2d, double *musum2d, double *psum2d)
+{
+    if (N < 2 || (N % 2) != 0 || L <= 0.0 || dk <= 0.0 || nk < 0 || nmu < 0)
+        return -1;
+    const int64_t NN = N;
+    const int64_t nblk = NN < 64 ? NN : 64;
+    const size_t n1 = (size_t)nk, n2 = nmu > 0 ? (size_t)nk * (size_t)nmu : 1;
+    const size_t per = 5 * n1 + 4 * n2;           /* one block's sums */
+    double *blk = (double *)calloc((size_t)nblk * per, sizeof(double));
+    if (!blk) return -2;
+    int64_t *cnt = (int64_t *)calloc((size_t)nblk * (n1 + n2), sizeof(int64_t));
+    if (!cnt) {
+        free(blk);
+        return -2;
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t b = 0; b < nblk; ++b) {
+        double *s = blk + (size_t)b * per;
+        int64_t *c = cnt + (size_t)b * (n1 + n2);
+        bin_rows(F1, F2, G1, G2, N, L, p, compensated, wsum, wsum_b, kmin, dk, nk, nmu,
+                 NN * b / nblk, NN * (b + 1) / nblk, c, s, s + n1, s + 2 * n1, s + 3 * n1,
+                 c + n1, s + 5 * n1, s + 5 * n1 + n2, s + 5 * n1 + 2 * n2);
+    }
+    for (int64_t b = 0; b < nblk; ++b) {
+        const double *s = blk + (size_t)b * per;
+        const int64_t *c = cnt + (size_t)b * (n1 + n2);
+        for (size_t k = 0; k < n1; ++k) {
+            modes1d[k] += c[k];
+            ksum1d[k] += s[k];
+            psum1d[k] += s[n1 + k];
+            p2sum1d[k] += s[2 * n1 + k];
+            p4sum1d[k] += s[3 * n1 + k];
+        }
+        if (nmu > 0) {
+            for (size_t k = 0; k < n2; ++k) {
+                modes2d[k] += c[n1 + k];
+                ksum2d[k] += s[5 * n1 + k];
+                musum2d[k] += s[5 * n1 + n2 + k];
+                psum2d[k] += s[5 * n1 + 2 * n2 + k];
+            }
+        }
+    }
+    free(blk);
+    free(cnt);
     return 0;
 }
 
@@ -357,4 +442,136 @@ int oracle_bin(const double *F1, const double *F2, int N, double L, int p,
 {
     return oracle_bin_pair(F1, F2, NULL, NULL, N, L, p, compensated, wsum, 1.0, kmin, dk, nk, nmu,
                            modes1d, ksum1d, psum1d, p2sum1d, p4sum1d, modes2d, ksum2d, musum2d, psum2d);
+}
+
+/* ---- the forward transform (Sec. 3.3.1: real field -> complex field) ----
+ *
+ * One-dimensional DFT X[k] = sum_{j<n} x[j] w_n^{j k}, w_n = exp(-2 pi i / n),
+ * by mixed-radix Cooley-Tukey decimation in time: with p the smallest prime
+ * factor of n and m = n / p, Y_r = DFT_m(x[r], x[r + p], x[r + 2p], ...) for
+ * r < p, and X[k] = sum_{r<p} w_n^{r k} Y_r[k mod m].  A prime n (m = 1) is
+ * therefore the direct sum.  Complex numbers are interleaved (re, im) doubles;
+ * tw[2e], tw[2e + 1] = cos, -sin (2 pi e / Ntw) for 0 <= e < Ntw, and n
+ * divides Ntw, so w_n^e = tw entry (e mod n) Ntw / n.  scratch holds 2 n
+ * doubles; the result goes to out[0 .. 2n). */
+static int smallest_prime_factor(int n)
+{
+    for (int p = 2; p * p <= n; ++p)
+        if (n % p == 0) return p;
+    return n;
+}
+
+static void dft_rec(const double *in, int64_t stride, int n, double *out, const double *tw, int Ntw,
+                    double *scratch)
+{
+    if (n == 1) {
+        out[0] = in[0];
+        out[1] = in[1];
+        return;
+    }
+    const int p = smallest_prime_factor(n), m = n / p;
+    for (int r = 0; r < p; ++r)                     /* the p decimated sub-transforms */
+        dft_rec(in + 2 * (int64_t)r * stride, stride * p, m, out + 2 * (int64_t)r * m, tw, Ntw, scratch);
+    const int64_t step = Ntw / n;
+    for (int k = 0; k < n; ++k) {
+        const int km = k % m;
+        double sr = 0.0, si = 0.0;
+        int64_t e = 0;                              /* e = r k mod n */
+        for (int r = 0; r < p; ++r) {
+            const double wr = tw[2 * e * step], wi = tw[2 * e * step + 1];
+            const double yr = out[2 * ((int64_t)r * m + km)], yi = out[2 * ((int64_t)r * m + km) + 1];
+            sr += wr * yr - wi * yi;
+            si += wr * yi + wi * yr;
+            e += k;
+            if (e >= n) e -= n;
+        }
+        scratch[2 * k] = sr;
+        scratch[2 * k + 1] = si;
+    }
+    memcpy(out, scratch, sizeof(double) * 2 * (size_t)n);
+}
+
+/* 1D transform of n complex values, in place in line[0 .. 2n); work holds 4 n doubles. */
+void oracle_dft_line(double *line, int n, const double *tw, double *work)
+{
+    dft_rec(line, 1, n, work, tw, n, work + 2 * (size_t)n);
+    memcpy(line, work, sizeof(double) * 2 * (size_t)n);
+}
+
+/* The twiddle table of length n (see above): tw[2n]. */
+void oracle_twiddles(int n, double *tw)
+{
+    for (int e = 0; e < n; ++e) {
+        const double a = 2.0 * M_PI * (double)e / (double)n;
+        tw[2 * e] = cos(a);
+        tw[2 * e + 1] = -sin(a);
+    }
+}
+
+/* r2c transform of mesh[N][N][N] (real, C order) into out[N][N][N/2+1]
+ * (complex interleaved): F~(i, j, l) = sum_c F[c] exp(-2 pi i (c_x i + c_y j
+ * + c_z l) / N), computed as 1D transforms along z (keeping l <= N/2), then
+ * y, then x.  Lines are independent and split over OpenMP threads.  Returns
+ * 0, or -1 on bad arguments, -2 if memory runs out. */
+int oracle_r2c(const double *mesh, int N, double *out)
+{
+    if (N < 1) return -1;
+    const int64_t NN = N, Nh = N / 2 + 1;
+    double *tw = (double *)malloc(sizeof(double) * 2 * (size_t)N);
+    if (!tw) return -2;
+    oracle_twiddles(N, tw);
+    int fail = 0;
+#pragma omp parallel
+    {
+        double *line = (double *)malloc(sizeof(double) * 6 * (size_t)N);
+        if (!line) {
+#pragma omp atomic write
+            fail = 1;
+        }
+        double *work = line ? line + 2 * (size_t)N : NULL;
+        /* z: real input lines, keep l = 0 .. N/2 */
+#pragma omp for schedule(static)
+        for (int64_t r = 0; r < NN * NN; ++r) {
+            if (!line) continue;
+            for (int64_t c = 0; c < NN; ++c) {
+                line[2 * c] = mesh[r * NN + c];
+                line[2 * c + 1] = 0.0;
+            }
+            oracle_dft_line(line, N, tw, work);
+            memcpy(out + 2 * r * Nh, line, sizeof(double) * 2 * (size_t)Nh);
+        }
+        /* y: lines (i, *, l) */
+#pragma omp for schedule(static)
+        for (int64_t r = 0; r < NN * Nh; ++r) {
+            if (!line) continue;
+            const int64_t i = r / Nh, l = r % Nh;
+            for (int64_t j = 0; j < NN; ++j) {
+                line[2 * j] = out[2 * ((i * NN + j) * Nh + l)];
+                line[2 * j + 1] = out[2 * ((i * NN + j) * Nh + l) + 1];
+            }
+            oracle_dft_line(line, N, tw, work);
+            for (int64_t j = 0; j < NN; ++j) {
+                out[2 * ((i * NN + j) * Nh + l)] = line[2 * j];
+                out[2 * ((i * NN + j) * Nh + l) + 1] = line[2 * j + 1];
+            }
+        }
+        /* x: lines (*, j, l) */
+#pragma omp for schedule(static)
+        for (int64_t r = 0; r < NN * Nh; ++r) {
+            if (!line) continue;
+            const int64_t j = r / Nh, l = r % Nh;
+            for (int64_t i = 0; i < NN; ++i) {
+                line[2 * i] = out[2 * ((i * NN + j) * Nh + l)];
+                line[2 * i + 1] = out[2 * ((i * NN + j) * Nh + l) + 1];
+            }
+            oracle_dft_line(line, N, tw, work);
+            for (int64_t i = 0; i < NN; ++i) {
+                out[2 * ((i * NN + j) * Nh + l)] = line[2 * i];
+                out[2 * ((i * NN + j) * Nh + l) + 1] = line[2 * i + 1];
+            }
+        }
+        free(line);
+    }
+    free(tw);
+    return fail ? -2 : 0;
 }

@@ -177,7 +177,13 @@ extern "C" pk_status pk_bin_static(const pk_config *cfg, const void *mesh, const
                                                                      c.dk, nk, mcap, cw, ph, kedge);
     e = cudaGetLastError();
     if (e != cudaSuccess) return static_fail(PK_ECUDA, cudaGetErrorString(e));
-    const int G = nsm < kMaxCtas ? nsm : kMaxCtas;
+    // As many CTAs as the plan path runs (bin_ctas_per_sm per SM), as far as
+    // their per-CTA histograms fit in the scratch (G * nh <= kMaxCtas * kMaxBins).
+    const long long fit = (long long)kMaxCtas * kMaxBins / bg.nh;
+    long long Gw = (long long)nsm * pk::bin_ctas_per_sm(bg, 0);
+    if (Gw > fit) Gw = fit;
+    if (Gw < 1) Gw = 1;
+    const int G = (int)Gw;
     const long long mesh_stride_c =
         mesh2 ? (long long)((reinterpret_cast<intptr_t>(mesh2) - reinterpret_cast<intptr_t>(mesh)) / 8) : 0;
     e = pk::launch_bin(mesh, 0, c.interlaced ? 1 : 0, 0, mesh_stride_c, 1, G, bg, cw, ph, kedge, partial, st);

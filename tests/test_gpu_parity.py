@@ -440,19 +440,51 @@ def _oracle_512(oracle, pos):
 
 # -------------------------------------- the 2048^3 Zel'dovich workload --
 
-def test_zeldovich_1024cubed_objects_pcs_interlaced_2048(pk, oracle, torch_mod):
+@pytest.fixture(scope="module")
+def zeldovich_1024cubed(torch_mod):
     """1024^3 objects on a Zel'dovich-displaced lattice (P ~ k^-2, rms 0.25
-    spacings), L = 2000, PCS + interlacing on N = 2048, FP32 mesh with int64
-    fixed-point paint, (k, mu) bins dk = 0.005 x 10, multipoles.  The oracle
-    cannot hold this mesh, so parity is checked on what it can compute at full
-    size: mass on both meshes, the painted field on sampled cell blocks, and
-    every mode count (bit-exact)."""
+    spacings), L = 2000, FP32 positions on the device (12.9 GB)."""
+    import synth
+    pos = synth.zeldovich_lattice(1024, 2000.0, synth.seed_for(3), device="cuda")
+    torch_mod.cuda.synchronize()
+    torch_mod.cuda.empty_cache()
+    yield pos
+    del pos
+    torch_mod.cuda.empty_cache()
+
+
+def with_raw(r):
+    """A GPU result used as the reference: add its pre-subtraction monopole."""
+    r = dict(r)
+    r["power_raw"] = r["power"] + r["shot_noise"]
+    return r
+
+
+def per_bin_errors(got, ref):
+    """Largest |got - ref| per quantity over the bins, relative to the
+    reference's pre-subtraction monopole of the bin (mode counts must agree)."""
+    assert np.array_equal(got["modes"], ref["modes"]) and np.array_equal(got["modes2d"], ref["modes2d"])
+    ok = ref["modes"] > 0
+    scale = ref["power_raw"][ok]
+    errs = {"P": float(np.max(np.abs(got["power"][ok] - ref["power"][ok]) / scale))}
+    for ell in range(3):
+        errs["P%d" % (2 * ell)] = float(np.max(np.abs(got["poles"][ell][ok] - ref["poles"][ell][ok]) / scale))
+    ok2 = ref["modes2d"] > 0
+    sc2 = np.broadcast_to(ref["power_raw"][:, None], ok2.shape)[ok2]
+    errs["Pkmu"] = float(np.max(np.abs(got["power2d"][ok2] - ref["power2d"][ok2]) / sc2))
+    return errs
+
+
+def test_zeldovich_1024cubed_objects_pcs_interlaced_2048(pk, oracle, torch_mod, zeldovich_1024cubed):
+    """1024^3 objects on a Zel'dovich-displaced lattice, PCS + interlacing on
+    N = 2048, FP32 mesh with int64 fixed-point paint, (k, mu) bins dk = 0.005
+    x 10, multipoles.  The painted field at full size: mass on both meshes,
+    sampled cell blocks against the oracle's block paint, and every mode count
+    (bit-exact)."""
     torch = torch_mod
     import ctypes
-    import synth
+    pos = zeldovich_1024cubed
     L, N, dk, nmu = 2000.0, 2048, 0.005, 10
-    pos = synth.zeldovich_lattice(1024, L, synth.seed_for(3), device="cuda")
-    torch.cuda.empty_cache()
     n = pos.shape[0]
     cfg = pk.make_config(L, N, "pcs", interlaced=True, dk=dk, nmu=nmu)
     plan = pk.pk_plan(cfg)
@@ -484,3 +516,43 @@ def test_zeldovich_1024cubed_objects_pcs_interlaced_2048(pk, oracle, torch_mod):
     assert r["wsum"] == float(n) and abs(r["shot_noise"] - L ** 3 / n) <= 1e-12 * L ** 3 / n
     assert np.all(np.isfinite(r["power"][ok])) and np.all(r["power"][ok] + r["shot_noise"] > 0)
     assert np.all(np.isfinite(r["poles"][:, ok]))
+
+
+def test_zeldovich_2048_fp32_form_per_bin_error_against_fp64_form(pk, torch_mod, zeldovich_1024cubed):
+    """The per-bin error of the precision form at scale.  The same 1024^3
+    objects, PCS + interlacing on N = 2048, in the FP32 form (int64 fixed-point
+    paint -> FP32 mesh -> R2C -> FP32 per-CTA bin partials -> FP64 sums) and in
+    the FP64 mesh form (FP64 mesh, D2Z, FP64 sums; itself held to 1e-6 of the
+    oracle in the tests above and at N = 1024 below).  The FP32 plan is
+    destroyed before the FP64 one (two FP64 2048^3 meshes take 137 GB).  Every
+    P(k), P(k, mu) and P_l bin must agree within 1e-4 of the bin's
+    pre-subtraction monopole."""
+    L, N, dk, nmu = 2000.0, 2048, 0.005, 10
+    pos = zeldovich_1024cubed
+    r32 = run_gpu(pk, pos, None, L, N, "pcs", True, dk, nmu=nmu, precision="f32")
+    torch_mod.cuda.empty_cache()
+    r64 = run_gpu(pk, pos, None, L, N, "pcs", True, dk, nmu=nmu, precision="f64")
+    torch_mod.cuda.empty_cache()
+    errs = per_bin_errors(r32, with_raw(r64))
+    print("2048^3 FP32 form vs FP64 form, max per-bin error / P_raw,0:", errs)
+    bad = {k: v for k, v in errs.items() if not v <= TOL["f32"]}
+    assert not bad, (bad, errs)
+
+
+def test_zeldovich_catalog_at_1024_against_the_oracle(pk, oracle, torch_mod, zeldovich_1024cubed):
+    """The oracle cannot hold a 2048^3 FP64 mesh pair plus its transforms on
+    the host, so it runs on the same 1.07e9-object catalog at N = 1024 (PCS +
+    interlacing, dk = 0.005 x 10 mu bins, multipoles): the FP32 form within
+    1e-4 and the FP64 mesh form within 1e-6 of each bin's pre-subtraction
+    monopole, mode counts bit-exact."""
+    L, N, dk, nmu = 2000.0, 1024, 0.005, 10
+    pos = zeldovich_1024cubed
+    got = {prec: run_gpu(pk, pos, None, L, N, "pcs", True, dk, nmu=nmu, precision=prec)
+           for prec in ("f32", "f64")}
+    torch_mod.cuda.empty_cache()
+    host = pos.cpu().double().numpy()
+    ref = oracle.fft_power(host, None, L, N, "pcs", True, True, dk=dk, nmu=nmu)
+    del host
+    for prec in ("f32", "f64"):
+        errs = compare(got[prec], ref, TOL[prec], nmu=nmu, ktol=1e-10)
+        print("1.07e9 objects at 1024^3, %s form vs oracle:" % prec, errs)

@@ -48,7 +48,20 @@ def brute_dft_r2c(mesh):
     return out
 
 
-@pytest.mark.parametrize("N", [6, 8])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 11, 12, 22, 33, 48, 64, 66])
+def test_dft_line_equals_direct_sum(oracle, n):
+    """The oracle's mixed-radix 1D transform (radix 2, 3 and a direct sum for
+    any other prime factor, as N = 40, 48, 528 need) equals the O(n^2)
+    definition X[k] = sum_j x[j] exp(-2 pi i j k / n) written out."""
+    rng = np.random.default_rng(100 + n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    j = np.arange(n)
+    ref = np.array([np.sum(x * np.exp(-2j * np.pi * j * k / n)) for k in range(n)])
+    got = oracle.dft(x)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("N", [6, 8, 12, 16])
 def test_r2c_equals_bruteforce_dft_and_parseval(oracle, N):
     rng = np.random.default_rng(7 + N)
     mesh = rng.standard_normal((N, N, N))
