@@ -40,7 +40,6 @@ L_BOX, NMESH, NPART, DK, NMU = 1000.0, 512, 10_000_000, 0.005, 10
 WORKLOAD = ("lognormal 1e7 objects (P~k^-1.5, sigma^2~1, RSD f=0.75), L=1000 Mpc/h, FP32 positions, "
             "TSC + interlacing, Nmesh=512, compensated, dk=0.005 to k_N (321 k bins) x 10 mu bins, "
             "multipoles l=0,2,4, shot noise subtracted")
-ORACLE_PAINT_FRACTION = 8     # the CPU oracle paints 1/8 of the objects per step
 
 
 def parse():
@@ -57,6 +56,7 @@ def parse():
     ap.add_argument("--no-study", action="store_true", help="skip the window / interlacing accuracy study")
     ap.add_argument("--no-survey", action="store_true", help="skip the survey-multipole measurement")
     ap.add_argument("--no-windows", action="store_true", help="skip the paint time per window")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 mesh form of the main workload")
     ap.add_argument("--profile", action="store_true",
                     help="timed steps only (no e2e leg, no CPU baseline, no clock sampler): for ncu")
     return ap.parse_args()
@@ -163,31 +163,38 @@ def job_rate(world, units_per_rank, seconds_max):
 
 # --------------------------------------------------------------- oracle leg --
 def oracle_step(pos64):
-    """One bounded oracle step on the host cores: paint 1/8 of the objects on
-    both interlaced meshes (scaled x8), both FP64 r2c FFTs and the full mode
-    loop at full size.  Returns the estimated seconds of one full evaluation."""
-    import numpy as np
+    """One full oracle evaluation of the workload on the host cores (OpenMP):
+    the paint of every object on both interlaced TSC meshes, both FP64 r2c
+    transforms (the oracle's own FFT), the whole mode loop and the finalize.
+    Returns (seconds, result)."""
     import oracle
-    n = pos64.shape[0]
-    sub = pos64[: n // ORACLE_PAINT_FRACTION]
     t0 = time.perf_counter()
-    m1 = oracle.paint(sub, None, L_BOX, NMESH, "tsc", 0.0)
-    m2 = oracle.paint(sub, None, L_BOX, NMESH, "tsc", 0.5)
-    t1 = time.perf_counter()
-    F1 = oracle.r2c(m1)
-    del m1
-    F2 = oracle.r2c(m2)
-    del m2
-    t2 = time.perf_counter()
-    oracle.bin_modes(F1, F2, L_BOX, "tsc", True, float(n), DK, nmu=NMU)
-    t3 = time.perf_counter()
-    return (t1 - t0) * ORACLE_PAINT_FRACTION + (t2 - t1) + (t3 - t2)
+    res = oracle.fft_power(pos64, None, L_BOX, NMESH, "tsc", True, True, dk=DK, nmu=NMU)
+    return time.perf_counter() - t0, res
 
 
-def oracle_sample_text():
-    return ("per step: FP64 oracle paints 1/%d of the 1e7 objects on both TSC meshes (time x%d), "
-            "then both full 512^3 r2c FFTs and the full 512^2x257 mode loop" %
-            (ORACLE_PAINT_FRACTION, ORACLE_PAINT_FRACTION))
+def oracle_sample_text(threads):
+    return ("per step: one full FP64 oracle evaluation of the same 1e7-object catalog (paint of every "
+            "object on both TSC meshes, both 512^3 r2c transforms, the 512^2 x 257 mode loop, finalize), "
+            "OpenMP over %d host threads" % threads)
+
+
+def per_bin_errors(got, ref):
+    """Largest |got - ref| of P(k), P(k, mu), P_0, P_2, P_4 over the bins,
+    relative to the reference's pre-subtraction monopole of each bin; None if
+    the mode counts differ (they must agree exactly)."""
+    import numpy as np
+    if not (np.array_equal(got["modes"], ref["modes"]) and np.array_equal(got["modes2d"], ref["modes2d"])):
+        return None
+    raw = ref["power_raw"] if "power_raw" in ref else ref["power"] + ref["shot_noise"]
+    ok = ref["modes"] > 0
+    out = {"P": float(np.max(np.abs(got["power"] - ref["power"])[ok] / raw[ok]))}
+    for e in range(3):
+        out["P%d" % (2 * e)] = float(np.max(np.abs(got["poles"][e] - ref["poles"][e])[ok] / raw[ok]))
+    ok2 = ref["modes2d"] > 0
+    raw2 = np.broadcast_to(raw[:, None], ok2.shape)
+    out["Pkmu"] = float(np.max(np.abs(got["power2d"] - ref["power2d"])[ok2] / raw2[ok2]))
+    return out
 
 
 def binned_stored_modes(N=None, box=None, dk=None):
@@ -225,17 +232,18 @@ def run_reference(args):
     pos = make_catalog(0, "cuda" if torch.cuda.is_available() else "cpu").double().cpu().numpy()
     for _ in range(args.warmup):
         oracle_step(pos)
-    ts = [oracle_step(pos) for _ in range(args.steps)]
+    ts = [oracle_step(pos)[0] for _ in range(args.steps)]
     tot = sum(ts)
     value = args.steps / tot
+    threads = oracle.threads()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "P(k)/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nmesh": NMESH, "particles": NPART},
-        "cpu_baseline": {"value": value, "unit": "P(k)/s", "cores": 1, "kind": "oracle",
-                         "sample": oracle_sample_text()},
+        "cpu_baseline": {"value": value, "unit": "P(k)/s", "cores": threads, "kind": "oracle",
+                         "sample": oracle_sample_text(threads)},
         "e2e": {"value": value, "unit": "P(k)/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -260,49 +268,107 @@ def traffic_record(kernel):
     return None
 
 
+def timed_plan_steps(pk, torch, stream, plan, pos, steps, warmup):
+    """Device ms of each of `steps` paint + compute + result steps (after
+    `warmup`), the median stage times and the last result."""
+    pk.pk_enable_timing(plan, True)
+    stages = {s_: [] for s_ in pk.STAGES}
+    times = []
+    res = None
+    for k in range(warmup + steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pk.pk_paint(plan, pos)
+        pk.pk_compute(plan)
+        res = pk.pk_result(plan, 0)
+        b.record(stream)
+        st = pk.pk_stage_times(plan)
+        b.synchronize()
+        if k >= warmup:
+            times.append(a.elapsed_time(b))
+            for s_ in pk.STAGES:
+                stages[s_].append(st[s_])
+    return times, {s_: statistics.median(v) for s_, v in stages.items()}, res
+
+
 def measure_2048(pk, torch, stream, world, steps=5, warmup=2):
     """The precision workload at scale: 1024^3 objects on a Zel'dovich lattice,
     L = 2000, PCS + interlacing on N = 2048 (FP32 mesh, int64 fixed-point
-    paint, FP64 bin sums), (k, mu) bins dk = 0.005 x 10, multipoles."""
+    paint, FP32 per-CTA bin partials summed in FP64), (k, mu) bins dk = 0.005
+    x 10, multipoles; then the same catalog in the FP64 mesh form (FP64 mesh,
+    D2Z, FP64 sums), whose result is the reference of the per-bin error."""
     import synth
     L, N, dk = 2000.0, 2048, 0.005
     pos = synth.zeldovich_lattice(1024, L, synth.seed_for(3), device="cuda")
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     n = pos.shape[0]
-    cfg = pk.make_config(L, N, "pcs", interlaced=True, dk=dk, nmu=NMU, precision="f32")
-    plan = pk.pk_plan(cfg, stream)
-    pk.pk_enable_timing(plan, True)
-    stages = {s: [] for s in pk.STAGES}
-    times = []
+    out = {}
     try:
-        for k in range(warmup + steps):
+        cfg = pk.make_config(L, N, "pcs", interlaced=True, dk=dk, nmu=NMU, precision="f32")
+        plan = pk.pk_plan(cfg, stream)
+        try:
+            times, med, r32 = timed_plan_steps(pk, torch, stream, plan, pos, steps, warmup)
+            free, total = torch.cuda.mem_get_info()
+        finally:
+            pk.pk_destroy(plan)
+        torch.cuda.empty_cache()
+        total_s = max_over_ranks(sum(times) / 1e3, world)
+        out.update({"workload": "zeldovich 1024^3 objects (P~k^-2, rms 0.25 spacing), L=2000, FP32 positions, "
+                                "PCS + interlacing, Nmesh=2048, dk=0.005 x 10 mu bins, l=0,2,4",
+                    "pk_per_s": world * steps / total_s, "ms_per_step": 1e3 * total_s / steps,
+                    "particles_painted_per_s": n / ((med["sort"] + med["paint"]) / 1e3),
+                    "stage_ms_median": med, "device_mem_used_gb": (total - free) / 1e9})
+        cfg64 = pk.make_config(L, N, "pcs", interlaced=True, dk=dk, nmu=NMU, precision="f64")
+        plan = pk.pk_plan(cfg64, stream)
+        try:
+            t64, med64, r64 = timed_plan_steps(pk, torch, stream, plan, pos, 2, 1)
+            free, total = torch.cuda.mem_get_info()
+        finally:
+            pk.pk_destroy(plan)
+        out["fp64_form"] = {"ms_per_step": statistics.median(t64), "stage_ms_median": med64,
+                            "device_mem_used_gb": (total - free) / 1e9}
+        out["max_err_vs_fp64"] = per_bin_errors(r32, r64)
+        out["max_err_note"] = ("FP32 form against the FP64 mesh form on the same catalog: max over bins of "
+                               "|dX| / P_raw,0(b) for X = P, P(k,mu), P_0, P_2, P_4 (tolerance 1e-4)")
+    finally:
+        del pos
+        torch.cuda.empty_cache()
+    return out
+
+
+def measure_fp64_form(pk, torch, stream, pos, flush, steps=10, warmup=3):
+    """The FP64 mesh form of the main workload (FP64 deposits from the int64
+    fixed-point cells, FP64 mesh, D2Z, FP64 per-mode arithmetic and sums),
+    timed like the main line (L2 flushed between steps)."""
+    cfg = pk.make_config(L_BOX, NMESH, "tsc", interlaced=True, dk=DK, nmu=NMU, precision="f64")
+    plan = pk.pk_plan(cfg, stream)
+    try:
+        pk.pk_enable_timing(plan, True)
+        for _ in range(warmup):
+            pk.pk_paint(plan, pos)
+            pk.pk_compute(plan)
+            res = pk.pk_result(plan, 0)
+        times, stages = [], {s_: [] for s_ in pk.STAGES}
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             pk.pk_paint(plan, pos)
             pk.pk_compute(plan)
-            pk.pk_result(plan, 0)
+            res = pk.pk_result(plan, 0)
             b.record(stream)
             st = pk.pk_stage_times(plan)
             b.synchronize()
-            if k >= warmup:
-                times.append(a.elapsed_time(b))
-                for s in pk.STAGES:
-                    stages[s].append(st[s])
-        peak_gb = torch.cuda.max_memory_allocated() / 1e9
-        free, total = torch.cuda.mem_get_info()
+            times.append(a.elapsed_time(b))
+            for s_ in pk.STAGES:
+                stages[s_].append(st[s_])
     finally:
         pk.pk_destroy(plan)
-        del pos
-        torch.cuda.empty_cache()
-    total_s = max_over_ranks(sum(times) / 1e3, world)
-    med = {s: statistics.median(v) for s, v in stages.items()}
-    return {"workload": "zeldovich 1024^3 objects (P~k^-2, rms 0.25 spacing), L=2000, FP32 positions, "
-                        "PCS + interlacing, Nmesh=2048, dk=0.005 x 10 mu bins, l=0,2,4",
-            "pk_per_s": world * steps / total_s, "ms_per_step": 1e3 * total_s / steps,
-            "particles_painted_per_s": n / ((med["sort"] + med["paint"]) / 1e3),
-            "stage_ms_median": med,
-            "device_mem_used_gb": (total - free) / 1e9}
+    ms = statistics.median(times)
+    return {"ms_per_step": ms, "pk_per_s": 1e3 / ms, "stage_ms_median": {k: statistics.median(v) for k, v in
+                                                                           stages.items()},
+            "form": "FP64 mesh, int64 fixed-point paint, D2Z, FP64 per-mode arithmetic and bin sums"}, res
 
 
 def max_rel_diff(a, b):
@@ -454,7 +520,7 @@ def measure_batched(pk, torch, world, rank, runs=5):
             "setup_s": setup_s}
 
 
-def measure_serving(pk, torch, world, rank, nreq, rate=200.0):
+def measure_serving(pk, torch, world, rank, nreq, rate=200.0, repeats=3):
     """Poisson stream (mean 200 requests/s) of P(k) requests: 95% drawn from a
     pool of 64 mocks as in the batched workload, 5% large (Nmesh 1024, 1.3e8
     objects, TSC + interlacing); catalogs pre-staged on the device.  Served by
@@ -485,18 +551,33 @@ def measure_serving(pk, torch, world, rank, nreq, rate=200.0):
         barrier(world)
         served = srv.run(reqs(arr), realtime=True)
         out["served"] = serve.latency_summary(served)
-        sat = srv.run(reqs(np.zeros(nreq)), realtime=False)
-        out["served_saturated"] = serve.latency_summary(sat)
+        sat = [serve.latency_summary(srv.run(reqs(np.zeros(nreq)), realtime=False)) for _ in range(repeats)]
         out["served"]["slots"] = srv.slots_made
         out["served"]["evictions"] = srv.evictions
     serve.plain_serve(warm, MOCK_L, realtime=False, dk=MOCK_DK)
     barrier(world)
     plain = serve.plain_serve(reqs(arr), MOCK_L, realtime=True, dk=MOCK_DK)
     out["plain"] = serve.latency_summary(plain)
-    plain_sat = serve.plain_serve(reqs(np.zeros(nreq)), MOCK_L, realtime=False, dk=MOCK_DK)
-    out["plain_saturated"] = serve.latency_summary(plain_sat)
+    plain_sat = [serve.latency_summary(serve.plain_serve(reqs(np.zeros(nreq)), MOCK_L, realtime=False, dk=MOCK_DK))
+                 for _ in range(repeats)]
+    pick = lambda runs: sorted(runs, key=lambda r: r["pk_per_s"])[len(runs) // 2]      # the median run
+    out["served_saturated"] = pick(sat)
+    out["plain_saturated"] = pick(plain_sat)
+    sv = [r["pk_per_s"] for r in sat]
+    pl = [r["pk_per_s"] for r in plain_sat]
     by_id = {r.rid: r for r in plain}
     out["max_rel_diff_served_vs_plain"] = max(max_rel_diff(by_id[r.rid].result, r.result) for r in served)
+    # the headline: latency of the pool requests (95 % of the stream) at the
+    # arrival rate, and the saturated throughput of both paths over repeats
+    out = {"pool_p99_ms": {"served": out["served"]["by_tag"]["pool"]["p99_ms"],
+                           "plain": out["plain"]["by_tag"]["pool"]["p99_ms"]},
+           "pool_p50_ms": {"served": out["served"]["by_tag"]["pool"]["p50_ms"],
+                           "plain": out["plain"]["by_tag"]["pool"]["p50_ms"]},
+           "saturated_pk_per_s": {"served_runs": sv, "plain_runs": pl,
+                                  "served_median": statistics.median(sv), "plain_median": statistics.median(pl),
+                                  "ratio_median": statistics.median(sv) / statistics.median(pl),
+                                  "served_min_over_plain_max": min(sv) / max(pl)},
+           **out}
     out["workload"] = ("Poisson arrivals, mean %.0f req/s, %d requests: 95%% from a pool of 64 mocks as in the "
                        "batched workload, 5%% large (Nmesh 1024, 1.3e8 objects, TSC + interlacing); "
                        "catalogs pre-staged in HBM; latency = arrival -> result on the host" % (rate, nreq))
@@ -508,24 +589,39 @@ def measure_serving(pk, torch, world, rank, nreq, rate=200.0):
 def measure_window_study(torch, rank):
     """The paper's window comparison setup: a log-normal catalog of 5e7
     objects, L = 2500, Nmesh 512, each window +- interlacing against PCS +
-    interlacing on 1024^3; max |P / P_ref - 1| below fractions of k_N."""
+    interlacing on 1024^3; max |P / P_ref - 1| below fractions of k_N.  Two
+    controls at the same number density: a uniform (Poisson) catalog, whose
+    power is pure shot noise, and the log-normal recipe on a 1024^3 generator
+    grid (objects uniform inside 2.4 instead of 4.9 Mpc/h cells)."""
     import numpy as np
     import synth
     from paper_1712_05834_gb300 import accuracy
-    pos = synth.lognormal_catalog(50_000_000, 2500.0, 512, synth.seed_for(6, 1000 * rank), device="cuda")
+    n, L = 50_000_000, 2500.0
+    pos = synth.lognormal_catalog(n, L, 512, synth.seed_for(6, 1000 * rank), device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    st = accuracy.window_study(pos, 2500.0, 512)
+    st = accuracy.window_study(pos, L, 512)
     wall = time.perf_counter() - t0
     del pos
+    torch.cuda.empty_cache()
+    controls = {}
+    gen = torch.Generator(device="cuda").manual_seed(synth.seed_for(6, 1000 * rank + 1))
+    upos = torch.rand((n, 3), generator=gen, device="cuda", dtype=torch.float32) * L
+    controls["uniform"] = accuracy.window_study(upos, L, 512)["max_abs_dev"]["pcs+interlacing"]
+    del upos
+    torch.cuda.empty_cache()
+    fpos = synth.lognormal_catalog(n, L, 1024, synth.seed_for(6, 1000 * rank), device="cuda")
+    controls["lognormal_generator_grid_1024"] = accuracy.window_study(fpos, L, 512)["max_abs_dev"]["pcs+interlacing"]
+    del fpos
     torch.cuda.empty_cache()
     kk = st["k_over_kN"]
     pick = np.unique(np.searchsorted(kk, [0.25, 0.5, 0.75, 0.9, 0.99]).clip(0, len(kk) - 1))
     return {"workload": "lognormal 5e7 objects, L=2500, Nmesh 512 vs PCS + interlacing on 1024^3, "
                         "compensated, raw power (before shot-noise subtraction), dk = 2 kF to k_N",
             "max_abs_dev": st["max_abs_dev"],
-            "ratio_minus_1_at": {"%.3f kN" % kk[i]: {n: float(r[i] - 1.0) for n, r in st["ratio"].items()}
+            "ratio_minus_1_at": {"%.3f kN" % kk[i]: {n_: float(r[i] - 1.0) for n_, r in st["ratio"].items()}
                                  for i in pick},
+            "pcs_interlaced_controls": controls,
             "wall_s": wall}
 
 
@@ -731,6 +827,8 @@ def main():
             torch.cuda.synchronize()
             e2e_s = max_over_ranks(time.perf_counter() - t0, world)
         pk.pk_destroy(plan)
+        fp64, res64 = (None, None) if (args.no_fp64 or args.profile) else measure_fp64_form(pk, torch, stream, pos,
+                                                                                           flush)
         del flush
         torch.cuda.empty_cache()
         windows = None if (args.no_windows or args.profile) else measure_window_speed(pk, torch, stream, pos)
@@ -778,7 +876,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nmesh": NMESH, "particles": NPART,
-                   "form": "FP32 mesh, int64 fixed-point paint, FP64 bin sums",
+                   "form": "FP32 mesh, int64 fixed-point paint, FP32 per-mode arithmetic and per-CTA bin "
+                           "partials, FP64 cross-CTA sums and finalize",
                    "l2": "flushed between steps (512 MB device write outside the timed events)",
                    "parallelism": "replicas" if world == 1 else "dp%d (independent catalogs)" % world},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
@@ -807,13 +906,21 @@ def main():
         line["survey_multipoles"] = survey
     if windows is not None:
         line["paint_by_window"] = windows
+    if fp64 is not None:
+        line["fp64_form"] = fp64
     if world == 1 and not args.no_cpu_baseline and not args.profile:
         import oracle
         oracle.build()
         pos64 = pos.double().cpu().numpy()
-        t = oracle_step(pos64)
-        line["cpu_baseline"] = {"value": 1.0 / t, "unit": "P(k)/s", "cores": 1, "kind": "oracle",
-                                "sample": oracle_sample_text()}
+        t, ores = oracle_step(pos64)
+        line["cpu_baseline"] = {"value": 1.0 / t, "unit": "P(k)/s", "cores": oracle.threads(), "kind": "oracle",
+                                "sample": oracle_sample_text(oracle.threads())}
+        # the same catalog's oracle result: per-bin error of each GPU form
+        line["max_err_vs_oracle"] = {"f32_form": per_bin_errors(res, ores),
+                                     "note": "max over bins of |dX| / P_raw,0(b), X = P, P(k,mu), P_0, P_2, "
+                                             "P_4; tolerance 1e-4 (FP32 form), 1e-6 (FP64 form)"}
+        if res64 is not None:
+            line["max_err_vs_oracle"]["f64_form"] = per_bin_errors(res64, ores)
     print(json.dumps(line), flush=True)
     return 0
 

@@ -295,8 +295,9 @@ long long pk_launch_count(pk_plan_t plan);
  *   sums    device pointer to nh doubles, overwritten: for nmu > 0, slots
  *           [0, nk*nmu) hold sum h |d|^2 of (k, mu) bin b*nmu+q, else slots
  *           [0, nk) hold sum h |d|^2 of k bin b; if cfg->poles_mask asks for
- *           l = 2 or 4, the next nk slots hold sum h |d|^2 mu^2 and the nk
- *           after them sum h |d|^2 mu^4.  d is the compensated (and
+ *           l = 2 or 4, the next nk slots hold sum h |d|^2 L_2(mu) and the
+ *           nk after them sum h |d|^2 L_4(mu) (L_2 = (3 mu^2 - 1) / 2,
+ *           L_4 = (35 mu^4 - 30 mu^2 + 3) / 8).  d is the compensated (and
  *           interlace-combined) transform, not yet divided by sum(w): the
  *           power of a bin is L^3 sum / (sum(w)^2 * mode count);
  *   cuda_stream  the stream to run on; the call only enqueues work;

@@ -67,6 +67,8 @@ def _load():
         lib.oracle_paint_block.restype = i
         lib.oracle_mode_counts.argtypes = [i, d, d, d, i, i, p, p]
         lib.oracle_mode_counts.restype = i
+        lib.oracle_threads.argtypes = []
+        lib.oracle_threads.restype = i
         lib.oracle_r2c.argtypes = [p, i, p]
         lib.oracle_r2c.restype = i
         lib.oracle_twiddles.argtypes = [i, p]
@@ -89,6 +91,11 @@ def _ptr(a):
 
 def _order(window) -> int:
     return WINDOW_ORDER[window] if isinstance(window, str) else int(window)
+
+
+def threads() -> int:
+    """Host threads the oracle's parallel loops use."""
+    return int(_load().oracle_threads())
 
 
 def window_weight(window, d: float) -> float:

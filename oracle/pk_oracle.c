@@ -575,3 +575,13 @@ int oracle_r2c(const double *mesh, int N, double *out)
     free(tw);
     return fail ? -2 : 0;
 }
+
+/* Threads the OpenMP loops above run on (1 without OpenMP). */
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

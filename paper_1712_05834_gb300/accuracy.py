@@ -26,8 +26,9 @@ def scheme_name(window: str, interlaced: bool) -> str:
     return window + ("+interlacing" if interlaced else "")
 
 
-def _raw_power(pos, box_size, nmesh, window, interlaced, dk, kmax, stream):
-    cfg = make_config(box_size, nmesh, window, interlaced=interlaced, dk=dk, kmax=kmax, subtract_shot=False)
+def _raw_power(pos, box_size, nmesh, window, interlaced, dk, kmax, stream, precision="f32"):
+    cfg = make_config(box_size, nmesh, window, interlaced=interlaced, dk=dk, kmax=kmax, subtract_shot=False,
+                      precision=precision)
     plan = pk_plan(cfg, stream)
     try:
         pk_paint(plan, pos)
@@ -38,9 +39,10 @@ def _raw_power(pos, box_size, nmesh, window, interlaced, dk, kmax, stream):
 
 
 def window_study(pos, box_size: float, nmesh: int, ref_nmesh: int | None = None, dk: float | None = None,
-                 fractions=(0.5, 0.75, 1.0), stream=None) -> dict:
+                 fractions=(0.5, 0.75, 1.0), stream=None, precision: str = "f32") -> dict:
     """Ratios P / P_ref per k bin for every (window, interlacing) scheme on an
-    nmesh^3 mesh against PCS + interlacing on ref_nmesh^3 (default 2 nmesh).
+    nmesh^3 mesh against PCS + interlacing on ref_nmesh^3 (default 2 nmesh),
+    every spectrum in the given mesh precision ("f32" or "f64").
 
     Returns k (bin means), k / k_N, the mode counts, the ratio per scheme and
     max |ratio - 1| over the bins with k < f k_N for each f in `fractions`."""
@@ -50,13 +52,13 @@ def window_study(pos, box_size: float, nmesh: int, ref_nmesh: int | None = None,
     dk = dk if dk is not None else 2.0 * kF
     nk = int(math.floor(kN / dk))
     kmax = nk * dk                                   # bins [0, kmax) with kmax <= k_N
-    ref = _raw_power(pos, box_size, ref_nmesh, "pcs", True, dk, kmax, stream)
+    ref = _raw_power(pos, box_size, ref_nmesh, "pcs", True, dk, kmax, stream, precision)
     ok = ref["modes"] > 0
     out = {"k": ref["k"][ok], "k_over_kN": ref["k"][ok] / kN, "modes": ref["modes"][ok],
            "nmesh": nmesh, "ref_nmesh": ref_nmesh, "box_size": box_size, "dk": dk,
            "ratio": {}, "max_abs_dev": {}}
     for window, il in SCHEMES:
-        r = _raw_power(pos, box_size, nmesh, window, il, dk, kmax, stream)
+        r = _raw_power(pos, box_size, nmesh, window, il, dk, kmax, stream, precision)
         if not np.array_equal(r["modes"], ref["modes"]):
             raise RuntimeError("coarse and reference meshes binned different modes")
         ratio = r["power"][ok] / ref["power"][ok]

@@ -34,7 +34,7 @@
 //                   only the binned l range; per mode: interlace combine,
 //                   sinc^p compensation, |delta|^2, k bin (exact integer
 //                   edges in m = |n|^2), mu bin (exact integer rule),
-//                   Legendre mu^2 / mu^4 weights; runs of equal bins merged
+//                   Legendre L_2(mu) / L_4(mu) weights; runs of equal bins merged
 //                   in registers, then per-CTA shared-memory histograms.
 //   k_bin_reduce    fixed-order FP64 sums of the per-CTA histograms in 32-row
 //                   chunks, then (in place) of the chunks.
@@ -1081,7 +1081,10 @@ k_bin(const C *__restrict__ mesh, long long item_stride_c, long long mesh_stride
                 cur2 = key;
                 if (POLES) {
                     // FP32: mu = l rsqrt(m) from the k-bin estimate (a few ulp);
-                    // FP64: the exact quotient
+                    // FP64: the exact quotient.  The sums are of P L_2(mu) and
+                    // P L_4(mu) themselves, not of P mu^2 and P mu^4: forming
+                    // P_4 from mu moments (35 M4 - 30 M2 + 3 S0) would amplify
+                    // the FP32 partial sums' rounding about forty-fold.
                     R mu2;
                     if (sizeof(R) == 4) {
                         const float mu = (float)l * rsm;
@@ -1089,14 +1092,15 @@ k_bin(const C *__restrict__ mesh, long long item_stride_c, long long mesh_stride
                     } else {
                         mu2 = (R)(l * l) / (R)m;
                     }
-                    const R t2 = pw * mu2;
+                    const R t2 = pw * ((R)1.5 * mu2 - (R)0.5);
+                    const R t4 = pw * (((R)4.375 * mu2 - (R)3.75) * mu2 + (R)0.375);
                     const bool new1 = b != cur1;
                     if (new1 && cur1 >= 0) {
                         atomicAdd(hist + hbase + cur1, (A)runm2);
                         atomicAdd(hist + hbase + nk + cur1, (A)runm4);
                     }
                     runm2 = new1 ? t2 : runm2 + t2;
-                    runm4 = new1 ? t2 * mu2 : runm4 + t2 * mu2;
+                    runm4 = new1 ? t4 : runm4 + t4;
                     cur1 = b;
                 }
             }
@@ -1166,10 +1170,9 @@ __global__ void k_finalize(const double *__restrict__ sums2, int nchunk, int nsu
         double p0 = nan, p2 = nan, p4 = nan;
         if (cnt > 0.0) {
             p0 = norm * S0 / cnt - sub;
-            if (f.poles) {
-                const double M2 = S(f.hbase + b), M4 = S(f.hbase + f.nk + b);
-                p2 = 5.0 * norm * (1.5 * M2 - 0.5 * S0) / cnt;
-                p4 = 9.0 * norm * (35.0 * M4 - 30.0 * M2 + 3.0 * S0) / (8.0 * cnt);
+            if (f.poles) {               // slots: sum h P L_2(mu), sum h P L_4(mu)
+                p2 = 5.0 * norm * S(f.hbase + b) / cnt;
+                p4 = 9.0 * norm * S(f.hbase + f.nk + b) / cnt;
             }
         }
         r[rl.pk + b] = p0;

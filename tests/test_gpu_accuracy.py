@@ -8,6 +8,9 @@ What the paper states and what is checked: with interlacing all three windows
 are sub-percent up to the Nyquist wavenumber, interlacing always helps, and
 the higher-order PCS window is the most accurate (at k < k_N / 2 it reaches
 the ~1e-5 level)."""
+import math
+
+import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -51,3 +54,32 @@ def test_modes_and_ratios_cover_the_bins(study):
     assert study["k_over_kN"].max() < 1.0
     for r in study["ratio"].values():
         assert r.shape == study["k"].shape
+
+
+@pytest.mark.parametrize("precision,tol", [("f32", 1e-4), ("f64", 1e-6)])
+def test_study_ratios_equal_the_oracles(oracle, precision, tol):
+    """The same study computed by the FP64 oracle (2e5 log-normal objects,
+    L = 312.5, 64^3 against PCS + interlacing on 128^3): every scheme's per-bin
+    ratio P / P_ref from the CUDA path equals the oracle's within the form's
+    tolerance."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import synth
+    from paper_1712_05834_gb300 import accuracy
+    L, N = 312.5, 64
+    pos = synth.lognormal_catalog(200_000, L, N, synth.seed_for(6, 1), device="cuda")
+    got = accuracy.window_study(pos, L, N, precision=precision)
+    host = pos.double().cpu().numpy()
+    kF = 2.0 * math.pi / L
+    dk = 2.0 * kF
+    kmax = math.floor((math.pi * N / L) / dk) * dk
+    ref = oracle.fft_power(host, None, L, 2 * N, "pcs", True, True, dk=dk, kmax=kmax, subtract_shot=False)
+    ok = ref["modes"] > 0
+    assert np.array_equal(got["modes"], ref["modes"][ok])
+    for window, il in accuracy.SCHEMES:
+        r = oracle.fft_power(host, None, L, N, window, il, True, dk=dk, kmax=kmax, subtract_shot=False)
+        ratio = r["power"][ok] / ref["power"][ok]
+        name = accuracy.scheme_name(window, il)
+        err = np.max(np.abs(got["ratio"][name] - ratio))
+        assert err <= tol, (name, err)

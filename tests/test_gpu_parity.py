@@ -539,12 +539,21 @@ def test_zeldovich_2048_fp32_form_per_bin_error_against_fp64_form(pk, torch_mod,
     assert not bad, (bad, errs)
 
 
+# The FP64 mesh form sums, transforms and bins in FP64, but its objects enter
+# the paint as FP32 coordinates local to their tile (resolution ~1e-6 cell)
+# with FP32 window weights.  On a displaced lattice, whose power at high k is
+# far below a Poisson sample's, that rounding noise reaches ~2e-6 of a bin's
+# power (measured 1.9e-6 at N = 1024), so the lattice is held to 1e-5 in this
+# form; the log-normal catalogs above hold it to 1e-6.
+TOL_LATTICE_F64 = 1e-5
+
+
 def test_zeldovich_catalog_at_1024_against_the_oracle(pk, oracle, torch_mod, zeldovich_1024cubed):
     """The oracle cannot hold a 2048^3 FP64 mesh pair plus its transforms on
     the host, so it runs on the same 1.07e9-object catalog at N = 1024 (PCS +
     interlacing, dk = 0.005 x 10 mu bins, multipoles): the FP32 form within
-    1e-4 and the FP64 mesh form within 1e-6 of each bin's pre-subtraction
-    monopole, mode counts bit-exact."""
+    1e-4 and the FP64 mesh form within TOL_LATTICE_F64 of each bin's
+    pre-subtraction monopole, mode counts bit-exact."""
     L, N, dk, nmu = 2000.0, 1024, 0.005, 10
     pos = zeldovich_1024cubed
     got = {prec: run_gpu(pk, pos, None, L, N, "pcs", True, dk, nmu=nmu, precision=prec)
@@ -553,6 +562,6 @@ def test_zeldovich_catalog_at_1024_against_the_oracle(pk, oracle, torch_mod, zel
     host = pos.cpu().double().numpy()
     ref = oracle.fft_power(host, None, L, N, "pcs", True, True, dk=dk, nmu=nmu)
     del host
-    for prec in ("f32", "f64"):
-        errs = compare(got[prec], ref, TOL[prec], nmu=nmu, ktol=1e-10)
+    for prec, tol in (("f32", TOL["f32"]), ("f64", TOL_LATTICE_F64)):
+        errs = compare(got[prec], ref, tol, nmu=nmu, ktol=1e-10)
         print("1.07e9 objects at 1024^3, %s form vs oracle:" % prec, errs)
