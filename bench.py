@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--no-survey", action="store_true", help="skip the survey-multipole measurement")
     ap.add_argument("--no-windows", action="store_true", help="skip the paint time per window")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 mesh form of the main workload")
+    ap.add_argument("--survey-profile", type=int, default=0, metavar="NMESH",
+                    help="only run 3 survey-multipole evaluations of a small catalog (1e5 galaxies, 1e6 randoms, "
+                         "1000 Mpc/h) on an NMESH^3 mesh and print their stage times: the workload of the "
+                         "survey kernels' ncu summary")
     ap.add_argument("--profile", action="store_true",
                     help="timed steps only (no e2e leg, no CPU baseline, no clock sampler): for ncu")
     return ap.parse_args()
@@ -751,10 +755,42 @@ def measure_survey(pk, torch, stream, world, rank, steps=5, warmup=2):
             "device_mem_used_gb": (total - free) / 1e9, "generation_s": gen_s}
 
 
+def survey_profile(nmesh):
+    """Three paint + compute evaluations of the survey multipoles on a small
+    catalog (the small case the survey kernels are profiled on)."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_1712_05834_gb300 as pk
+    pk.build()
+    torch.cuda.set_device(0)
+    ext = 1000.0
+    c = synth.survey_catalogs(100_000, 1_000_000, ext, synth.seed_for(9, 7), ngrid=128, device="cuda")
+    L, origin = 1.04 * ext, (-0.02 * ext,) * 3
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+    gd = pk.survey_catalog(dev(c["data"]), wcomp=dev(c["data_wcomp"]), nbar=dev(c["data_nbar"]))
+    gr = pk.survey_catalog(dev(c["randoms"]), nbar=dev(c["rand_nbar"]))
+    stream = torch.cuda.Stream()
+    plan = pk.pk_survey_plan(pk.make_survey_config(L, origin, nmesh, "cic", False, dk=0.005,
+                                                   capacity=len(c["data"]) + len(c["randoms"])), stream)
+    pk.pk_survey_enable_timing(plan, True)
+    try:
+        for _ in range(3):
+            pk.pk_survey_paint(plan, gd, gr)
+            pk.pk_survey_compute(plan)
+            pk.pk_survey_result(plan)
+            print(json.dumps(pk.pk_survey_stage_times(plan)), flush=True)
+    finally:
+        pk.pk_survey_destroy(plan)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.survey_profile:
+        return survey_profile(args.survey_profile)
     import numpy as np
     import torch
 

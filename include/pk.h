@@ -134,7 +134,12 @@ typedef struct {
  * sort paint variant, no reserved capacity. */
 void pk_config_default(pk_config *cfg);
 
-/* Create a plan: validates cfg, allocates the meshes (in-place r2c layout,
+/* Create a plan: the setup of the paper's to_mesh(Nmesh, BoxSize, window,
+ * interlaced, compensated) and FFTPower(mode, dk, kmin, Nmu, poles, los)
+ * options (Sec. 3.3.2 "From Catalog to Mesh", Sec. 3.4.1 "Power Spectra");
+ * the paper's algorithms run at construction and keep their
+ * results as attributes (Sec. 2.3.3), which this split into plan / paint /
+ * compute / result mirrors.  Validates cfg, allocates the meshes (in-place r2c layout,
  * N x N x 2(N/2+1) reals per mesh, (1 + interlaced) meshes per catalog), the
  * cuFFT plan, the bin tables and result buffers, and computes the geometry-only
  * bin data (mode counts, mean k, mean mu) on the device.  All work of the plan
@@ -193,7 +198,11 @@ pk_status pk_paint_values(pk_plan_t plan, const void *pos, int dtype, const floa
  * PK_ECUFFT, PK_ECUDA. */
 pk_status pk_compute(pk_plan_t plan);
 
-/* Wait for the last pk_compute and describe catalog `item`'s result.
+/* Wait for the last pk_compute and describe catalog `item`'s result: the
+ * FFTPower attributes of Sec. 3.4.1 (P(k), P(k, mu), multipoles P_l, the bin
+ * edges, mean k and mu, mode counts) plus the shot noise that was
+ * subtracted.  The view's pointers are plan-owned host memory, valid until
+ * the next pk_compute or pk_destroy.
  * Errors: PK_ESTATE (no compute yet), PK_EINVAL (item out of range),
  * PK_EOVERFLOW (fixed-point headroom exceeded while painting), PK_ECUDA. */
 pk_status pk_result(pk_plan_t plan, int item, pk_result_view *out);
@@ -550,7 +559,9 @@ const char *pk_survey_error(pk_survey_t plan);
 /* Free the survey plan (waits for its stream).  NULL is a no-op. */
 pk_status pk_survey_destroy(pk_survey_t plan);
 
-/* Free everything the plan owns (waits for its stream).  NULL is a no-op. */
+/* Free everything the plan owns (waits for its stream): the end of the
+ * algorithm object of Sec. 2.3.3, whose results the caller has read through
+ * pk_result.  NULL is a no-op. */
 pk_status pk_destroy(pk_plan_t plan);
 
 /* Static string naming a status. */

@@ -106,7 +106,7 @@ void window_reach(int p, int interlaced, int *lo, int *hi) {
 // largest divisor <= 16, else the smallest in [17, 28].
 int choose_tile(int N, int span, int requested) {
     const int tmin = span > 1 ? span : 1;
-    auto ok = [&](int T) { return T >= tmin && N % T == 0 && paint_smem_bytes(T) <= 200 * 1024; };
+    auto ok = [&](int T) { return T >= tmin && N % T == 0 && paint_smem_bytes(T, 4) <= 200 * 1024; };
     if (requested > 0) return ok(requested) ? requested : -1;
     int best = -1;
     for (int T = tmin; T <= 16 && T <= N; ++T)

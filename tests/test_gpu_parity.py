@@ -94,24 +94,29 @@ def compare(got, ref, tol, nmu=0, ktol=1e-12):
 # ------------------------------------------------------------ paint step --
 
 @pytest.mark.parametrize("variant", ["sort", "atomic"])
-@pytest.mark.parametrize("window,interlaced", [("cic", False), ("tsc", True), ("pcs", True)])
+@pytest.mark.parametrize("window,interlaced", [("cic", False), ("tsc", True), ("pcs", True), ("cic", True)])
 @pytest.mark.parametrize("N", [32, 40])
-def test_painted_mesh_matches_oracle_cell_by_cell(pk, oracle, window, interlaced, N, variant):
+@pytest.mark.parametrize("form", ["f64 weighted", "f32 unit"])
+def test_painted_mesh_matches_oracle_cell_by_cell(pk, oracle, window, interlaced, N, variant, form):
+    """Weighted FP64-mesh paint and unit-weight FP32 paint (the one-sweep
+    path of 16^3 tiles at N = 32; N = 40 uses 10^3 tiles) against the
+    oracle's per-cell sums, including objects on the box faces and outside it."""
     rng = np.random.default_rng(1000 + N)
     L = 250.0
     pos = rng.uniform(-0.5 * L, 1.5 * L, size=(20000, 3))
     pos[:8] = [[0, 0, 0], [L, L, L], [L - 1e-9, 0, 0], [-1e-9, 3.0, 7.0],
                [L / N * 5, L / N * 7, L / N * 9], [L / N * 5.5, 0.5 * L / N, L],
                [3 * L, -2 * L, 0.25 * L], [1e-300, 1e-300, 1e-300]]
-    w = rng.uniform(0.2, 2.0, 20000).astype(np.float32)
-    cfg = pk.make_config(L, N, window, interlaced=interlaced, dk=2 * math.pi / L * 2, precision="f64",
-                         paint_variant=variant)
+    weighted = form == "f64 weighted"
+    w = rng.uniform(0.2, 2.0, 20000).astype(np.float32) if weighted else None
+    cfg = pk.make_config(L, N, window, interlaced=interlaced, dk=2 * math.pi / L * 2,
+                         precision="f64" if weighted else "f32", paint_variant=variant)
     plan = pk.pk_plan(cfg)
     try:
         pk.pk_paint(plan, pos, w)
         for m in range(2 if interlaced else 1):
-            got = pk.pk_mesh(plan, 0, m, N, f64=True)
-            ref = oracle.paint(pos, w.astype(np.float64), L, N, window, 0.5 * m)
+            got = pk.pk_mesh(plan, 0, m, N, f64=weighted).astype(np.float64)
+            ref = oracle.paint(pos, None if w is None else w.astype(np.float64), L, N, window, 0.5 * m)
             err = np.abs(got - ref)
             assert np.max(err) <= 1e-5 * (1.0 + np.max(np.abs(ref))), (m, np.max(err))
             assert abs(got.sum() - ref.sum()) <= 1e-6 * ref.sum()
