@@ -71,11 +71,6 @@ constexpr int kUploadChunk = 256;     // int64 values per parameter upload (2 KB
 // tile) were measured faster with deposits that skip cells outside the tile.
 constexpr int kFlatMaxCand = 640;
 
-__device__ __forceinline__ int wrapmod(int a, int n) {
-    int r = a % n;
-    return r < 0 ? r + n : r;
-}
-
 // Cell coordinate s = x * (N / L) wrapped periodically into [0, N).  Written
 // with explicitly rounded intrinsics so that no FMA contraction can differ
 // between the count and the scatter kernels: both must see the same s.
@@ -610,6 +605,9 @@ __device__ __forceinline__ double cell_value<double>(unsigned lo, unsigned hi, u
     return __ll2double_rn((long long)a64) * (double)inv_scale;
 }
 
+// 2^k for -126 <= k <= 127, exactly (the fixed-point scales: S <= 40, B <= 22).
+__device__ __forceinline__ float pow2f(int k) { return __uint_as_float((unsigned)(127 + k) << 23); }
+
 __device__ __forceinline__ int ceil_log2(unsigned x) {     // x >= 1
     return x <= 1u ? 0 : 32 - __clz(x - 1u);
 }
@@ -760,12 +758,17 @@ k_paint_tiles(const float4 *__restrict__ sorted, const uint32_t *__restrict__ of
     unsigned long long *acc64 = reinterpret_cast<unsigned long long *>(smu);
     float4 *cand = reinterpret_cast<float4 *>(smu + 2 * T3);
 
-    const int64_t gt = blockIdx.x;                    // item * ntiles + tile
-    const int64_t item = gt / g.ntiles;
-    const int64_t t = gt - item * g.ntiles;
-    const int tx = (int)(t / ((int64_t)g.ntx * g.ntx));
-    const int ty = (int)((t / g.ntx) % g.ntx);
-    const int tz = (int)(t % g.ntx);
+    // item * ntiles + tile (the launch keeps the block count below 2^31, so
+    // 32-bit unsigned division suffices: 64-bit division is a long software
+    // sequence that every thread of every tile would run)
+    const unsigned gt = blockIdx.x;
+    const unsigned ntiles = (unsigned)g.ntiles, ntx = (unsigned)g.ntx;
+    const unsigned item = gt / ntiles;
+    const unsigned t = gt - item * ntiles;
+    const unsigned tq = t / ntx;
+    const int tz = (int)(t - tq * ntx);
+    const int tx = (int)(tq / ntx);
+    const int ty = (int)(tq - (unsigned)tx * ntx);
 
     // Segments: neighbour offset d (per axis -1, 0, +1) with the classes of
     // that neighbour whose window reaches this tile: d = -1 -> class 2,
@@ -779,8 +782,11 @@ k_paint_tiles(const float4 *__restrict__ sorted, const uint32_t *__restrict__ of
         const int dy = ay == 0 ? -1 : (ay == 4 ? 1 : 0), cy = ay == 0 ? 2 : (ay == 4 ? 0 : ay - 1);
         const int dz = az - 1;
         const int cz0 = dz == -1 ? 2 : 0, cz1 = dz == 1 ? 0 : 2;
-        const int64_t nt = ((int64_t)wrapmod(tx + dx, g.ntx) * g.ntx + wrapmod(ty + dy, g.ntx)) * g.ntx +
-                           wrapmod(tz + dz, g.ntx);
+        const int n = g.ntx;
+        const int wx = tx + dx < 0 ? tx + dx + n : (tx + dx >= n ? tx + dx - n : tx + dx);
+        const int wy = ty + dy < 0 ? ty + dy + n : (ty + dy >= n ? ty + dy - n : ty + dy);
+        const int wz = tz + dz < 0 ? tz + dz + n : (tz + dz >= n ? tz + dz - n : tz + dz);
+        const int64_t nt = ((int64_t)wx * n + wy) * n + wz;
         const int64_t kb = ((int64_t)item * g.ntiles + nt) * kClasses + cx * 9 + cy * 3;
         const uint32_t b = off[kb + cz0], e = off[kb + cz1 + 1];
         s_beg[s] = b;
@@ -816,16 +822,16 @@ k_paint_tiles(const float4 *__restrict__ sorted, const uint32_t *__restrict__ of
         sp.twoB = __uint_as_float((unsigned)(127 + max(sp.B, 0)) << 23);
         sp.twoB_u = 1u << max(sp.B, 0);
         sp.inv2B = __uint_as_float((unsigned)(127 - max(sp.B, 0)) << 23);
-        sp.hi_scale = ldexpf(1.0f, sp.B - S);
+        sp.hi_scale = pow2f(sp.B - S);
         const float wmax = __uint_as_float(wmax_bits[item]);
-        const float hmax = ldexpf(wmax, S - sp.B);
+        const float hmax = wmax * pow2f(S - sp.B);
         sp.fast = sp.B >= 1 && hmax < 4194304.0f && (float)nc * (hmax + 1.0f) < 2.0e9f;
         // wmax_deposit > 0: all weights are in [0, wmax_deposit / max W]; then
         // no deposit reaches 2^B if wmax_deposit 2^S < 2^B - 1
-        if (sp.fast && wmax_deposit > 0.0f && ldexpf(wmax_deposit, S) < (float)(sp.twoB_u - 1u)) sp.fast = 2;
+        if (sp.fast && wmax_deposit > 0.0f && wmax_deposit * pow2f(S) < (float)(sp.twoB_u - 1u)) sp.fast = 2;
     }
-    const float scale = ldexpf(1.0f, S);
-    const float inv_scale = ldexpf(1.0f, -S);
+    const float scale = pow2f(S);
+    const float inv_scale = pow2f(-S);
     // With no split needed (unit weights, sparse tile) the tile is painted in
     // one sweep over its candidates, each read once straight from the sorted
     // copy (nothing to stage), with branch-free deposits; an interlaced pair
