@@ -177,6 +177,27 @@ def oracle_step(pos64):
     return time.perf_counter() - t0, res
 
 
+def oracle_tiny():
+    """The oracle on the tiny plain workload (1e5 uniform objects, FP64
+    positions, L = 1000, CIC on 64^3, dk = 0.01, shot noise subtracted) on all
+    host threads and on one, a few evaluations each (median seconds)."""
+    import oracle
+    import synth
+    pos = synth.uniform_catalog(100_000, 1000.0, synth.seed_for(1))
+    out = {"workload": "1e5 uniform objects, CIC, Nmesh 64, dk 0.01 (20 k bins)"}
+    allc = oracle.threads()
+    for label, nt in (("all_cores", allc), ("one_core", 1)):
+        oracle.set_threads(nt)
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            oracle.fft_power(pos, None, 1000.0, 64, "cic", False, True, dk=0.01)
+            ts.append(time.perf_counter() - t0)
+        out[label] = {"threads": nt, "s_per_pk": statistics.median(ts), "pk_per_s": 1.0 / statistics.median(ts)}
+    oracle.set_threads(allc)
+    return out
+
+
 def oracle_sample_text(threads):
     return ("per step: one full FP64 oracle evaluation of the same 1e7-object catalog (paint of every "
             "object on both TSC meshes, both 512^3 r2c transforms, the 512^2 x 257 mode loop, finalize), "
@@ -957,6 +978,7 @@ def main():
                                              "P_4; tolerance 1e-4 (FP32 form), 1e-6 (FP64 form)"}
         if res64 is not None:
             line["max_err_vs_oracle"]["f64_form"] = per_bin_errors(res64, ores)
+        line["cpu_baseline"]["tiny_workload"] = oracle_tiny()
     print(json.dumps(line), flush=True)
     return 0
 

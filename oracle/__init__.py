@@ -69,6 +69,8 @@ def _load():
         lib.oracle_mode_counts.restype = i
         lib.oracle_threads.argtypes = []
         lib.oracle_threads.restype = i
+        lib.oracle_set_threads.argtypes = [i]
+        lib.oracle_set_threads.restype = None
         lib.oracle_r2c.argtypes = [p, i, p]
         lib.oracle_r2c.restype = i
         lib.oracle_twiddles.argtypes = [i, p]
@@ -96,6 +98,11 @@ def _order(window) -> int:
 def threads() -> int:
     """Host threads the oracle's parallel loops use."""
     return int(_load().oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    """Use n host threads in the oracle's parallel loops from now on."""
+    _load().oracle_set_threads(int(n))
 
 
 def window_weight(window, d: float) -> float:

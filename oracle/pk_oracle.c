@@ -585,3 +585,13 @@ int oracle_threads(void)
     return 1;
 #endif
 }
+
+/* Run the OpenMP loops above on n threads from now on (n >= 1). */
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
