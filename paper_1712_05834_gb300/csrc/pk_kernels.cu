@@ -473,24 +473,23 @@ __device__ __forceinline__ void deposit_flat(unsigned *sm, int cell0, unsigned t
     }
 }
 
-// ---- one-sweep paint of 16^3 tiles (unit weights) ----
+// ---- one-sweep paint of 16^3 tiles into a padded layout (unit weights, PCS) ----
 // Shared layout: cell (x, y, z) of the tile's mesh m at word
 //   m * kWords + x * kXS + y * kYS + kZlo + z,
-// where every row of z holds a halo [-kZlo, T + kYS - kZlo - T) wide enough
-// for every deposit of every candidate of the tile (objects of the tile and
-// the boundary classes of its neighbours, both meshes), so a deposit needs no
-// bounds test along z; a row outside the tile along x or y is redirected as a
-// whole to the trash row that follows the mesh's rows (never flushed).  Each
-// deposit is then one FFMA, one IADD and one 32-bit shared atomic at an
-// immediate offset from its row.
+// where every row of z holds a halo [-kZlo, kYS - kZlo) wide enough for every
+// deposit of every candidate of the tile (objects of the tile and the
+// boundary classes of its neighbours, both meshes), so a deposit needs no
+// bounds test along z; a row outside the tile along x or y is skipped by a
+// predicate (a word shared by many lanes of one atomic instruction would
+// serialize them).  Each deposit is then one FFMA, one IADD and one 32-bit
+// shared atomic at an immediate offset from its row.
 template <int P>
 struct SweepLayout {
     static constexpr int T = 16;
     static constexpr int Zlo = P == 2 ? 2 : 4;        // z halo below the tile
     static constexpr int YS = P == 2 ? 20 : 24;       // row stride (even: paired flush loads)
     static constexpr int XS = T * YS;                 // plane stride
-    static constexpr int Trash = T * XS;              // first word of the trash row
-    static constexpr int Words = T * XS + YS;         // one mesh with its trash row
+    static constexpr int Words = T * XS;              // one mesh (a multiple of 4 words)
     static constexpr int BzMin = -Zlo, BzMax = YS - Zlo - P;
 };
 
@@ -502,7 +501,7 @@ struct SweepLayout {
 template <int P, bool SKIP_PLANES>
 __device__ __forceinline__ void sweep_deposit(unsigned *sm, float x, float y, float z, float ws) {
     using Lay = SweepLayout<P>;
-    constexpr int kOut = 1 << 20;                     // > Trash: marks a row outside the tile
+    constexpr int kOut = 1 << 20;                     // > Words: marks a row outside the tile
     int bx, by, bz;
     float wx[P], wy[P], wz[P];
     spline_weights<P>(x, bx, wx);
@@ -523,7 +522,7 @@ __device__ __forceinline__ void sweep_deposit(unsigned *sm, float x, float y, fl
         for (int b = 0; b < P; ++b) {
             const float vxy = vxw * wy[b];
             const int ro = ox[a] + oy[b];
-            if (ro < Lay::Trash) {           // a row inside the tile (no deposit otherwise)
+            if (ro < Lay::Words) {           // a row inside the tile (no deposit otherwise)
                 unsigned *row = sm + ro;
 #pragma unroll
                 for (int c = 0; c < P; ++c)
