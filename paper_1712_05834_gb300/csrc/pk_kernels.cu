@@ -1413,8 +1413,11 @@ __global__ void k_geom_finalize(BinGeom g, const int *__restrict__ kedge, double
 }
 
 template <typename K>
+// Raise a kernel's dynamic shared-memory limit when the launch may pass the
+// 48 KB default together with the kernel's static shared arrays (a few KB at
+// most here), so an exactly-48 KB dynamic request is covered too.
 cudaError_t set_smem(K kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
+    if (bytes <= 40 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
