@@ -262,12 +262,27 @@ pk_status pk_projected(pk_plan_t plan, int item, unsigned keep_axes, pk_projecte
  * transformed or never painted), PK_EINVAL (item / mesh out of range), PK_ECUDA. */
 pk_status pk_mesh(pk_plan_t plan, int item, int mesh, void *dst);
 
+/* Choose the 3D r2c transform of pk_compute (the Fourier transform of the
+ * painted field, Sec. 3.3.1; the binning it feeds, Sec. 3.4.1).  on = 1: the
+ * library's own FFT kernels -- length-N complex FFTs along y and x of the mesh
+ * with each z row read as N/2 complex pairs (d[2n] + i d[2n+1], in place),
+ * then one pass that takes the length-N/2 FFTs along z, splits the packed
+ * transform into the r2c transform and bins it without writing it.  on = 0:
+ * cuFFT's in-place R2C, then the bin pass.  Both give the same result within
+ * FP32 rounding.  The own transform is the default where it applies: the FP32
+ * mesh form with nmesh 256 or 512.  After a compute with it, pk_cross
+ * and pk_projected first write the r2c transform into the meshes (one extra
+ * pass).  Takes effect at the next pk_compute.
+ * Errors: PK_EINVAL (on = 1 where the own transform does not apply). */
+pk_status pk_use_own_fft(pk_plan_t plan, int on);
+
 /* Stages whose device time pk_stage_times reports. */
 typedef enum {
     PK_STAGE_SORT = 0,    /* tile count + scan + scatter (pk_paint)             */
     PK_STAGE_PAINT = 1,   /* shared-memory tile paint (pk_paint)                */
-    PK_STAGE_FFT = 2,     /* cuFFT r2c of every mesh (pk_compute)               */
-    PK_STAGE_BIN = 3,     /* compensate + interlace + bin (pk_compute)          */
+    PK_STAGE_FFT = 2,     /* r2c of every mesh: cuFFT, or the own y and x passes */
+    PK_STAGE_BIN = 3,     /* compensate + interlace + bin (own transform: with   */
+                          /* the z FFTs and the r2c split)                       */
     PK_STAGE_FINAL = 4,   /* histogram reduce + normalize + multipoles          */
     PK_NSTAGES = 5
 } pk_stage;

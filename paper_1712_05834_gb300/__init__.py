@@ -40,7 +40,7 @@ __all__ = [
     "PK_PAINT_SORT", "PK_PAINT_ATOMIC",
     "PkError", "pk_config", "pk_config_default", "make_config", "pk_plan", "pk_paint",
     "pk_paint_many", "pk_compute", "pk_result", "pk_mesh", "pk_destroy", "pk_status_string",
-    "pk_last_error", "pk_enable_timing", "pk_stage_times", "pk_launch_count", "FFTPower", "load",
+    "pk_last_error", "pk_enable_timing", "pk_stage_times", "pk_launch_count", "pk_use_own_fft", "FFTPower", "load",
     "build", "make_survey_config", "survey_catalog", "pk_survey_plan", "pk_survey_paint", "pk_survey_compute",
     "pk_survey_result", "pk_survey_ylm", "pk_survey_destroy", "ConvolvedFFTPower", "pk_survey_bounds",
     "survey_box",
@@ -55,7 +55,7 @@ VARIANTS = {"sort": PK_PAINT_SORT, "atomic": PK_PAINT_ATOMIC}
 WINDOWS = {"cic": PK_CIC, "tsc": PK_TSC, "pcs": PK_PCS}
 EXPORTED = ["pk_config_default", "pk_plan", "pk_paint", "pk_paint_many", "pk_compute",
             "pk_result", "pk_mesh", "pk_destroy", "pk_status_string", "pk_last_error",
-            "pk_plan_error", "pk_enable_timing", "pk_stage_times", "pk_launch_count",
+            "pk_plan_error", "pk_enable_timing", "pk_stage_times", "pk_launch_count", "pk_use_own_fft",
             "pk_bin_static", "pk_cross", "pk_cross_result", "pk_paint_values", "pk_projected", "pk_lognormal_plan", "pk_lognormal_field", "pk_lognormal_draw",
             "pk_lognormal_amp", "pk_lognormal_launch_count", "pk_lognormal_error", "pk_lognormal_destroy",
             "pk_survey_config_default", "pk_survey_plan", "pk_survey_paint", "pk_survey_compute",
@@ -180,6 +180,8 @@ def load():
         lib.pk_plan_error.restype = ctypes.c_char_p
         lib.pk_enable_timing.argtypes = [vp, i]
         lib.pk_enable_timing.restype = i
+        lib.pk_use_own_fft.argtypes = [vp, i]
+        lib.pk_use_own_fft.restype = i
         lib.pk_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
         lib.pk_stage_times.restype = i
         lib.pk_launch_count.argtypes = [vp]
@@ -433,6 +435,12 @@ def pk_mesh(plan, item, mesh, nmesh, f64=False):
 
 def pk_enable_timing(plan, on=True):
     _check(load().pk_enable_timing(plan, int(bool(on))), plan)
+
+
+def pk_use_own_fft(plan, on=True):
+    """Select the r2c transform of the next pk_compute: the library's own FFT
+    kernels (y and x passes, then z fused into the bin pass) or cuFFT's R2C."""
+    _check(load().pk_use_own_fft(plan, int(bool(on))), plan)
 
 
 def pk_stage_times(plan) -> dict:

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpk.so")
-SOURCES = ["pk_kernels.cu", "pk_api.cu", "pk_static.cu", "pk_lognormal.cu", "pk_survey.cu"]
+SOURCES = ["pk_kernels.cu", "pk_api.cu", "pk_static.cu", "pk_lognormal.cu", "pk_survey.cu", "pk_fft.cu"]
 HEADERS = [os.path.join(ROOT, "include", "pk.h"), os.path.join(CSRC, "pk_internal.h"),
            os.path.join(CSRC, "pk_plan.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

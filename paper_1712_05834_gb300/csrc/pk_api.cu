@@ -70,7 +70,7 @@ void free_plan(pk_plan_s *p) {
     void *dev[] = {p->mesh, p->d_count, p->d_off, p->d_scan_tmp, p->d_rank, p->d_sorted,
                    p->d_stage, p->d_item_off, p->d_wsums, p->d_wmax, p->d_cw, p->d_ph,
                    p->d_kedge, p->d_partial, p->d_sums2, p->d_res, p->d_modes1d, p->d_modes2d,
-                   p->d_err, p->d_acc, p->fft_work, p->d_xres, p->d_proj};
+                   p->d_err, p->d_acc, p->fft_work, p->d_xres, p->d_proj, p->d_tw};
     for (void *d : dev)
         if (d) cudaFree(d);
     if (p->h_res) cudaFreeHost(p->h_res);
@@ -385,6 +385,17 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
         PK_CUDA(P, cudaMemcpy(P->d_kedge, P->kedge.data(), sizeof(int) * (nk + 1), cudaMemcpyHostToDevice));
     }
 
+    // ---- own transform: FP32 meshes of the supported sizes use it by default ----
+    if (!P->f64 && own_fft_supported(P->N)) {
+        std::vector<float> tw(2 * (size_t)P->N);
+        own_fft_twiddles(P->N, tw.data());
+        PK_CUDA(P, dev_alloc(&P->d_tw, sizeof(float) * tw.size()));
+        PK_CUDA(P, cudaMemcpy(P->d_tw, tw.data(), sizeof(float) * tw.size(), cudaMemcpyHostToDevice));
+        // one wave of k_zbin CTAs, within the partial histograms k_bin's grid sized
+        P->G_own = std::min(P->G_total, P->nsm * zbin_ctas_per_sm(bg, c.interlaced));
+        P->own_fft = 1;
+    }
+
     // ---- geometry-only bin data: exact counts, mean k, mean mu ----
     {
         const size_t hn = (size_t)bg.mhi * nq + 1;
@@ -520,6 +531,7 @@ static pk_status paint_atomic(pk_plan_s *P, const void *dpos, int dtype, const f
     P->launches += launches;
     P->npainted = nitems;
     P->transformed = 0;
+    P->zpacked = 0;
     return PK_OK;
 }
 
@@ -630,6 +642,7 @@ static pk_status paint_impl(pk_plan_s *P, const void *pos, int dtype, const floa
     P->launches += launches;
     P->npainted = nitems;
     P->transformed = 0;
+    P->zpacked = 0;
     return PK_OK;
 }
 
@@ -667,7 +680,22 @@ pk_status pk_compute(pk_plan_t P) {
     const int cap = capturing(st);
     const int tm = P->timing && !cap;
     if (tm) PK_CUDA(P, cudaEventRecord(P->tev[3], st));
-    if (P->fft_single) {
+    const int nitems = P->npainted;
+    const long long item_c = (long long)P->nm * P->mesh_reals / 2;   // complex elements
+    const long long mesh_c = P->mesh_reals / 2;
+    int G = std::max(1, P->G_total / nitems);
+    if (P->own_fft) {
+        // x and y passes, then z fused into the bin pass: the meshes end up
+        // holding the x/y transforms of the packed z rows (zpacked)
+        G = std::max(1, P->G_own / nitems);
+        PK_CUDA(P, launch_fft_xy(P->mesh, nitems * P->nm, mesh_c, P->N, P->d_tw, st));
+        P->transformed = 1;
+        P->zpacked = 1;
+        if (tm) PK_CUDA(P, cudaEventRecord(P->tev[4], st));
+        PK_CUDA(P, launch_zbin(P->mesh, P->cfg.interlaced, item_c, mesh_c, nitems, G, P->bg, P->d_cw, P->d_ph,
+                               P->d_tw, P->d_kedge, P->d_partial, st));
+        P->launches += 2;   // the two axis passes
+    } else if (P->fft_single) {
         PK_CUFFT(P, transform_meshes(P, P->mesh, P->npainted * P->nm));
     } else {
         // the painted catalogs: the whole-batch plan, else the binary digits of
@@ -691,14 +719,13 @@ pk_status pk_compute(pk_plan_t P) {
         }
         if (left != 0) return fail(P, PK_ECUFFT, "internal: catalog count not covered by the FFT plans");
     }
-    P->transformed = 1;
-    if (tm) PK_CUDA(P, cudaEventRecord(P->tev[4], st));
-    const int nitems = P->npainted;
-    const int G = std::max(1, P->G_total / nitems);
-    const long long item_c = (long long)P->nm * P->mesh_reals / 2;   // complex elements
-    const long long mesh_c = P->mesh_reals / 2;
-    PK_CUDA(P, launch_bin(P->mesh, P->f64, P->cfg.interlaced, item_c, mesh_c, nitems, G, P->bg,
-                          P->d_cw, P->d_ph, P->d_kedge, P->d_partial, st));
+    if (!P->own_fft) {
+        P->transformed = 1;
+        P->zpacked = 0;
+        if (tm) PK_CUDA(P, cudaEventRecord(P->tev[4], st));
+        PK_CUDA(P, launch_bin(P->mesh, P->f64, P->cfg.interlaced, item_c, mesh_c, nitems, G, P->bg,
+                              P->d_cw, P->d_ph, P->d_kedge, P->d_partial, st));
+    }
     if (tm) PK_CUDA(P, cudaEventRecord(P->tev[5], st));
     PK_CUDA(P, launch_bin_reduce(P->d_partial, P->f64, G, P->bg.nh, nitems, P->d_sums2, st));
     PK_CUDA(P, launch_finalize(P->d_sums2, G, P->d_modes1d, P->d_modes2d, P->d_wsums, P->d_err, P->fg,
@@ -720,6 +747,28 @@ pk_status pk_compute(pk_plan_t P) {
 
 static pk_status fill_view(pk_plan_s *P, const double *r, pk_result_view *out);
 
+// After a compute on the own transform the meshes hold the x/y transforms of
+// the packed z rows; the passes that read the r2c transform itself get it
+// written in place first (once per compute).
+static pk_status finish_transform(pk_plan_s *P) {
+    if (!P->zpacked) return PK_OK;
+    const long long item_c = (long long)P->nm * P->mesh_reals / 2;
+    PK_CUDA(P, launch_zfinish(P->mesh, P->cfg.interlaced, item_c, P->mesh_reals / 2, P->computed, P->N, P->d_tw,
+                              P->nsm, P->st));
+    P->launches += 1;
+    P->zpacked = 0;
+    return PK_OK;
+}
+
+pk_status pk_use_own_fft(pk_plan_t P, int on) {
+    if (!P) return PK_EINVAL;
+    P->err.clear();
+    if (on && !P->d_tw)
+        return fail(P, PK_EINVAL, "the own transform needs the FP32 mesh form and nmesh 256 or 512");
+    P->own_fft = on ? 1 : 0;
+    return PK_OK;
+}
+
 pk_status pk_result(pk_plan_t P, int item, pk_result_view *out) {
     if (!P) return PK_EINVAL;
     P->err.clear();
@@ -737,6 +786,7 @@ pk_status pk_cross(pk_plan_t P, int item_a, int item_b) {
     if (item_a < 0 || item_a >= P->computed || item_b < 0 || item_b >= P->computed)
         return fail(P, PK_EINVAL, "item out of range");
     const cudaStream_t st = P->st;
+    if (pk_status s = finish_transform(P); s != PK_OK) return s;
     const long long item_c = (long long)P->nm * P->mesh_reals / 2;   // complex elements per catalog
     const long long mesh_c = P->mesh_reals / 2;
     const size_t csz = 2 * P->esz;
@@ -776,6 +826,7 @@ pk_status pk_projected(pk_plan_t P, int item, unsigned keep_axes, pk_projected_v
     if (!P->transformed || P->computed < 1) return fail(P, PK_ESTATE, "pk_projected needs a pk_compute first");
     if (item < 0 || item >= P->computed) return fail(P, PK_EINVAL, "item out of range");
     const cudaStream_t st = P->st;
+    if (pk_status s = finish_transform(P); s != PK_OK) return s;
     const int nk = P->bg.nk;
     const size_t csz = 2 * P->esz;
     const size_t item_bytes = (size_t)P->nm * P->mesh_reals * P->esz;

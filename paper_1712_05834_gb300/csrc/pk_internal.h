@@ -121,6 +121,23 @@ cudaError_t launch_plane_bin(const void *m1, const void *m2, int f64, int N, int
                              const void *ph, const int *kedge, int nk, double kF, double *sums, int nsm,
                              cudaStream_t st);
 
+// ---- own FFT path (pk_fft.cu), FP32 meshes with N in {256, 512} ----
+// The meshes' z rows are read as N/2 complex values (packed real pairs).
+bool own_fft_supported(int N);
+void own_fft_twiddles(int N, float *tw);          // tw[2e], tw[2e+1] = W_N^e, e < N
+// length-N FFTs along y, then along x, of nmesh packed meshes mesh_c complex apart
+cudaError_t launch_fft_xy(void *mesh, int nmesh, long long mesh_c, int N, const void *tw, cudaStream_t st);
+// z transform + r2c split + the bin pass of launch_bin (FP32 form), partial
+// histograms as launch_bin writes them
+cudaError_t launch_zbin(const void *mesh, int interlaced, long long item_stride_c, long long mesh_stride_c,
+                        int nitems, int ctas_per_item, const BinGeom &g, const void *cw, const void *ph,
+                        const void *tw, const int *kedge, void *partial, cudaStream_t st);
+size_t zbin_smem_bytes(const BinGeom &g, int interlaced);
+int zbin_ctas_per_sm(const BinGeom &g, int interlaced);
+// z transform + r2c split written back in place (the meshes then hold the r2c transform)
+cudaError_t launch_zfinish(void *mesh, int interlaced, long long item_stride_c, long long mesh_stride_c,
+                           int nitems, int N, const void *tw, int nsm, cudaStream_t st);
+
 cudaError_t launch_geom_hist(const BinGeom &g, unsigned long long *H, unsigned long long *HL,
                              cudaStream_t st);
 cudaError_t launch_geom_finalize(const BinGeom &g, const int *kedge, double kF,

@@ -32,6 +32,11 @@ struct pk_plan_s {
     std::vector<cufftHandle> fft;
     int fft_single = 0;              // one single-mesh plan, one call per mesh (large meshes)
     void *fft_work = nullptr;
+    // Own transform (pk_fft.cu): y and x passes, then z fused into the bin.
+    int own_fft = 0;                 // pk_compute uses it (FP32 form, supported N)
+    int zpacked = 0;                 // meshes hold the x/y transforms of packed z rows
+    int G_own = 0;                   // k_zbin CTAs for one catalog
+    void *d_tw = nullptr;            // W_N^e, e < N (float2)
 
     uint32_t *d_count = nullptr;     // objects per (tile, class) key
     uint32_t *d_off = nullptr;       // exclusive scan of d_count (+ total)
