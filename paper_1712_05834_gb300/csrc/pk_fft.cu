@@ -24,7 +24,9 @@
 //                    transform after a compute (cross and projected power).
 // All transforms are forward (e^{-2 pi i jk/n}), unnormalized, radix-8
 // decimation in frequency with a radix-4 step where the length needs one;
-// twiddles come from one table W_N^e (e < N) computed in FP64 on the host.
+// twiddles come from one table W_N^e (e < N) computed in FP64 on the host
+// (the x and y passes read W^n and W^{4n} of a butterfly from it and form
+// its other twiddles as products, a few ulp each).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -35,7 +37,7 @@ namespace pk {
 
 namespace {
 
-constexpr int kAxisThreads = 256;
+constexpr int kAxisThreads = 512;   // x / y passes: two 68 KB tiles of 16 warps per SM
 constexpr int kZVec = 4;              // consecutive modes per lane in the bin step
 
 __device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -141,8 +143,24 @@ __device__ __forceinline__ void axis_step(float2 *buf, float2 *g, long long astr
             const int beta = grp + NG * s;
             const int n = beta % Q, base = (beta / Q) * S + n;
             dft<R>(v[s]);
+            {
+                constexpr int E = LEN / S;
+                float2 ww[R];
+                ww[1] = tw[n * E];
+                if constexpr (R == 8) {
+                    ww[4] = tw[4 * n * E];
+                    ww[2] = c_mul(ww[1], ww[1]);
+                    ww[3] = c_mul(ww[2], ww[1]);
+                    ww[5] = c_mul(ww[4], ww[1]);
+                    ww[6] = c_mul(ww[4], ww[2]);
+                    ww[7] = c_mul(ww[4], ww[3]);
+                } else {
+                    ww[2] = tw[2 * n * E];
+                    ww[3] = c_mul(ww[2], ww[1]);
+                }
 #pragma unroll
-            for (int k = 1; k < R; ++k) v[s][k] = c_mul(v[s][k], tw[n * k * (LEN / S)]);   // W_S^{nk}
+                for (int k = 1; k < R; ++k) v[s][k] = c_mul(v[s][k], ww[k]);
+            }
 #pragma unroll
             for (int k = 0; k < R; ++k) buf[(base + Q * k) * NB + c] = v[s][k];
         }
@@ -152,7 +170,7 @@ __device__ __forceinline__ void axis_step(float2 *buf, float2 *g, long long astr
 }
 
 template <int LEN, int NB>
-__global__ void __launch_bounds__(kAxisThreads)
+__global__ void __launch_bounds__(kAxisThreads, 2)
 k_fft_axis(float2 *__restrict__ mesh, long long mesh_c, long long outer_stride, long long astride,
            const float2 *__restrict__ twg) {
     extern __shared__ __align__(16) unsigned char smraw[];
