@@ -23,7 +23,7 @@
 //                    into the rows in place, for the passes that read the
 //                    transform after a compute (cross and projected power).
 // All transforms are forward (e^{-2 pi i jk/n}), unnormalized, radix-8
-// decimation in frequency with a radix-4 step where the length needs one;
+// decimation in frequency with radix-4 steps where the length needs them;
 // twiddles come from one table W_N^e (e < N) computed in FP64 on the host
 // (the x and y passes read W^n and W^{4n} of a butterfly from it and form
 // its other twiddles as products, a few ulp each).
@@ -88,17 +88,21 @@ __device__ __forceinline__ void dft<8>(float2 *v) {
 // power of two >= 4): 8, with 4 for the blocks of 16 and 4 points.
 __host__ __device__ constexpr int radix_of(int S) { return (S == 4 || S == 16) ? 4 : 8; }
 
+// Radix order of the z FFTs: as radix_of, but 4 for the blocks of 32 (a
+// length-256 transform runs 8, 4, 8).
+__host__ __device__ constexpr int zradix_of(int S) { return S == 32 ? 4 : radix_of(S); }
+
 // Frequency at position p (< S) after all steps over a block of S points:
 // a step of radix R puts output k of the butterfly at n + (S/R) k, so the
 // digits of p, most significant first, are the frequency's digits from the
 // least significant up.
-template <int S, int MUL>
+template <int S, int MUL, bool Z = false>
 __device__ __forceinline__ int dif_freq(int p) {
     if constexpr (S == 1) {
         return 0;
     } else {
-        constexpr int R = radix_of(S), Q = S / R;
-        return (p / Q) * MUL + dif_freq<Q, MUL * R>(p % Q);
+        constexpr int R = Z ? zradix_of(S) : radix_of(S), Q = S / R;
+        return (p / Q) * MUL + dif_freq<Q, MUL * R, Z>(p % Q);
     }
 }
 
@@ -207,8 +211,10 @@ cudaError_t axis_inst(float2 *mesh, int nmesh, long long mesh_c, const float2 *t
 // shared buffer, RS slots each; position p sits in slot p ^ ((p >> 2) & 15),
 // a bijection on [0, M] that keeps the FFT steps, the natural-order write and
 // the bin loop's lane patterns (kZVec consecutive modes per lane, ascending
-// and mirrored) free of bank conflicts, except the middle step of the
-// length-256 FFT (two-way).  Tables indexed by l use the same slots.
+// and mirrored) free of bank conflicts, except the reads of the last step of
+// the length-256 FFT (two-way; radix order 8, 4, 8 -- the order 8, 8, 4 had
+// its middle step's reads and writes two-way).  Tables indexed by l use the
+// same slots.
 __device__ __forceinline__ int zslot(int p) { return p ^ ((p >> 2) & 15); }
 
 template <int M>
@@ -222,16 +228,16 @@ struct ZRows {
 // lanes of a step read consecutive or equal entries.
 __host__ __device__ constexpr int ztw_offset(int M, int S) {
     int off = 0;
-    for (int s = M; s > S; s /= radix_of(s)) {
-        const int q = s / radix_of(s);
-        off += q > 1 ? (radix_of(s) - 1) * q : 0;
+    for (int s = M; s > S; s /= zradix_of(s)) {
+        const int q = s / zradix_of(s);
+        off += q > 1 ? (zradix_of(s) - 1) * q : 0;
     }
     return off;
 }
 
 __device__ __forceinline__ void fill_ztw(float2 *ztw, const float2 *__restrict__ twg, int M) {
-    for (int s = M; s > 1; s /= radix_of(s)) {
-        const int R = radix_of(s), Q = s / R, off = ztw_offset(M, s);
+    for (int s = M; s > 1; s /= zradix_of(s)) {
+        const int R = zradix_of(s), Q = s / R, off = ztw_offset(M, s);
         if (Q == 1) continue;
         for (int e = threadIdx.x; e < (R - 1) * Q; e += blockDim.x) {
             const int k = e / Q + 1, n = e % Q;
@@ -254,7 +260,7 @@ template <int M, int NR, int S, bool FIRST>
 __device__ __forceinline__ void zfft_step(float2 *rows, const float2 *m1, const float2 *m2, long long offA,
                                           long long offB, const float2 *ztw, int lane) {
     constexpr int RS = ZRows<M>::RS;
-    constexpr int R = radix_of(S), Q = S / R;
+    constexpr int R = zradix_of(S), Q = S / R;
     constexpr int BPR = M / R;                    // butterflies per row
     constexpr int TOT = NR * BPR;
     constexpr int PER = (TOT + 31) / 32;
@@ -292,7 +298,7 @@ __device__ __forceinline__ void zfft_step(float2 *rows, const float2 *m1, const 
                 for (int k = 0; k < R; ++k) rows[r * RS + zslot(base + Q * k)] = v[s][k];
             } else {
 #pragma unroll
-                for (int k = 0; k < R; ++k) rows[r * RS + zslot(dif_freq<M, 1>(base + k))] = v[s][k];
+                for (int k = 0; k < R; ++k) rows[r * RS + zslot(dif_freq<M, 1, true>(base + k))] = v[s][k];
             }
         }
     }
