@@ -151,6 +151,7 @@ void pk::set_plan_error(const char *msg) { g_plan_error = msg ? msg : ""; }
 // single-mesh plan, else one call of the plan over one catalog's meshes
 // (count must then be nm).
 cufftResult pk::transform_meshes(pk_plan_s *P, void *first, int count) {
+    if (ensure_cufft(P) != PK_OK) return CUFFT_ALLOC_FAILED;
     if (!P->fft_single && count != P->nm) return CUFFT_INVALID_VALUE;
     const int calls = P->fft_single ? count : 1;
     for (int k = 0; k < calls; ++k) {
@@ -165,6 +166,48 @@ cufftResult pk::transform_meshes(pk_plan_s *P, void *first, int count) {
         if (r != CUFFT_SUCCESS) return r;
     }
     return CUFFT_SUCCESS;
+}
+
+// cuFFT plans of a plan's meshes (in-place r2c): over 1, 2, 4, ... catalogs and
+// all B, or one single-mesh plan; one shared work area, the plan's stream.
+// Made when the plan is built unless the own transform serves it, else on
+// first use (pk_use_own_fft(plan, 0), or transform_meshes for the survey
+// passes), so a 2048^3 plan on the own transform holds no cuFFT work area.
+pk_status pk::ensure_cufft(pk_plan_s *P) {
+    if (!P->fft.empty()) return PK_OK;
+    if (capturing(P->st)) return fail(P, PK_ESTATE, "cuFFT plans cannot be made under stream capture");
+    {
+        // Meshes above 512^3 are transformed one per call: at 1024^3 a plan
+        // batched over two meshes took 18.4 ms against 10.9 ms for two
+        // single-mesh calls (equal at 512^3, where batching helps small meshes).
+        P->fft_single = P->N > kSingleFftAbove;
+        P->fft_items.clear();
+        if (P->fft_single) {
+            P->fft_items.push_back(1);
+        } else {
+            for (int c = 1; c < P->B; c <<= 1) P->fft_items.push_back(c);
+            P->fft_items.push_back(P->B);
+        }
+        long long n[3] = {P->N, P->N, P->N};
+        long long inembed[3] = {P->N, P->N, 2LL * P->Nh};
+        long long onembed[3] = {P->N, P->N, (long long)P->Nh};
+        size_t work_max = 0;
+        for (int c : P->fft_items) {
+            cufftHandle h;
+            PK_CUFFT(P, cufftCreate(&h));
+            P->fft.push_back(h);
+            PK_CUFFT(P, cufftSetAutoAllocation(h, 0));
+            size_t work = 0;
+            PK_CUFFT(P, cufftMakePlanMany64(h, 3, n, inembed, 1, P->mesh_reals, onembed, 1, P->mesh_reals / 2,
+                                            P->f64 ? CUFFT_D2Z : CUFFT_R2C,
+                                            P->fft_single ? 1LL : (long long)c * P->nm, &work));
+            work_max = std::max(work_max, work);
+        }
+        PK_CUDA(P, dev_alloc(&P->fft_work, work_max));
+        for (cufftHandle h : P->fft) PK_CUFFT(P, cufftSetWorkArea(h, P->fft_work));
+        for (cufftHandle h : P->fft) PK_CUFFT(P, cufftSetStream(h, P->st));
+    }
+    return PK_OK;
 }
 
 extern "C" {
@@ -385,7 +428,7 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
         PK_CUDA(P, cudaMemcpy(P->d_kedge, P->kedge.data(), sizeof(int) * (nk + 1), cudaMemcpyHostToDevice));
     }
 
-    // ---- own transform: FP32 meshes of the supported sizes use it by default ----
+    // ---- own transform: FP32 meshes of the supported sizes (the default at 256, 512, 2048) ----
     if (!P->f64 && own_fft_supported(P->N)) {
         std::vector<float> tw(2 * (size_t)P->N);
         own_fft_twiddles(P->N, tw.data());
@@ -393,7 +436,7 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
         PK_CUDA(P, cudaMemcpy(P->d_tw, tw.data(), sizeof(float) * tw.size(), cudaMemcpyHostToDevice));
         // one wave of k_zbin CTAs, within the partial histograms k_bin's grid sized
         P->G_own = std::min(P->G_total, P->nsm * zbin_ctas_per_sm(bg, c.interlaced));
-        P->own_fft = 1;
+        P->own_fft = own_fft_default(P->N) ? 1 : 0;
     }
 
     // ---- geometry-only bin data: exact counts, mean k, mean mu ----
@@ -451,36 +494,6 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
         PK_CUDA(P, cudaMemcpy(P->d_modes1d, P->modes1d.data(), 8 * nk, cudaMemcpyHostToDevice));
     }
 
-    // ---- cuFFT: in-place r2c; plans over 1, 2, 4, ... catalogs and all B, or one single-mesh plan ----
-    {
-        // Meshes above 512^3 are transformed one per call: at 1024^3 a plan
-        // batched over two meshes took 18.4 ms against 10.9 ms for two
-        // single-mesh calls (equal at 512^3, where batching helps small meshes).
-        P->fft_single = P->N > kSingleFftAbove;
-        if (P->fft_single) {
-            P->fft_items.push_back(1);
-        } else {
-            for (int c = 1; c < P->B; c <<= 1) P->fft_items.push_back(c);
-            P->fft_items.push_back(P->B);
-        }
-        long long n[3] = {P->N, P->N, P->N};
-        long long inembed[3] = {P->N, P->N, 2LL * P->Nh};
-        long long onembed[3] = {P->N, P->N, (long long)P->Nh};
-        size_t work_max = 0;
-        for (int c : P->fft_items) {
-            cufftHandle h;
-            PK_CUFFT(P, cufftCreate(&h));
-            P->fft.push_back(h);
-            PK_CUFFT(P, cufftSetAutoAllocation(h, 0));
-            size_t work = 0;
-            PK_CUFFT(P, cufftMakePlanMany64(h, 3, n, inembed, 1, P->mesh_reals, onembed, 1, P->mesh_reals / 2,
-                                            P->f64 ? CUFFT_D2Z : CUFFT_R2C,
-                                            P->fft_single ? 1LL : (long long)c * P->nm, &work));
-            work_max = std::max(work_max, work);
-        }
-        PK_CUDA(P, dev_alloc(&P->fft_work, work_max));
-        for (cufftHandle h : P->fft) PK_CUFFT(P, cufftSetWorkArea(h, P->fft_work));
-    }
     return PK_OK;
 }
 
@@ -498,11 +511,12 @@ pk_status pk_plan(const pk_config *cfg, void *cuda_stream, pk_plan_t *out) {
         return s;
     }
     P->st = reinterpret_cast<cudaStream_t>(cuda_stream);
-    for (cufftHandle h : P->fft) {
-        if (cufftSetStream(h, P->st) != CUFFT_SUCCESS) {
-            g_plan_error = "cufftSetStream failed";
+    if (!P->own_fft) {
+        s = ensure_cufft(P);
+        if (s != PK_OK) {
+            g_plan_error = P->err;
             free_plan(P);
-            return PK_ECUFFT;
+            return s;
         }
     }
     *out = P;
@@ -684,6 +698,7 @@ pk_status pk_compute(pk_plan_t P) {
     const long long item_c = (long long)P->nm * P->mesh_reals / 2;   // complex elements
     const long long mesh_c = P->mesh_reals / 2;
     int G = std::max(1, P->G_total / nitems);
+    pk_status s_ = PK_OK;
     if (P->own_fft) {
         // x and y passes, then z fused into the bin pass: the meshes end up
         // holding the x/y transforms of the packed z rows (zpacked)
@@ -695,6 +710,8 @@ pk_status pk_compute(pk_plan_t P) {
         PK_CUDA(P, launch_zbin(P->mesh, P->cfg.interlaced, item_c, mesh_c, nitems, G, P->bg, P->d_cw, P->d_ph,
                                P->d_tw, P->d_kedge, P->d_partial, st));
         P->launches += 2;   // the two axis passes
+    } else if ((s_ = ensure_cufft(P)) != PK_OK) {
+        return s_;
     } else if (P->fft_single) {
         PK_CUFFT(P, transform_meshes(P, P->mesh, P->npainted * P->nm));
     } else {
@@ -764,7 +781,10 @@ pk_status pk_use_own_fft(pk_plan_t P, int on) {
     if (!P) return PK_EINVAL;
     P->err.clear();
     if (on && !P->d_tw)
-        return fail(P, PK_EINVAL, "the own transform needs the FP32 mesh form and nmesh 256 or 512");
+        return fail(P, PK_EINVAL, "the own transform needs the FP32 mesh form and nmesh 256, 512, 1024 or 2048");
+    if (!on) {
+        if (pk_status s = ensure_cufft(P); s != PK_OK) return s;
+    }
     P->own_fft = on ? 1 : 0;
     return PK_OK;
 }

@@ -89,4 +89,6 @@ namespace pk {
 // r2c of `count` consecutive meshes of the plan's layout starting at `first`
 // (batched plans: count must equal the meshes of one catalog).
 cufftResult transform_meshes(pk_plan_s *P, void *first, int count);
+// Make the plan's cuFFT plans if they do not exist yet (not under stream capture).
+pk_status ensure_cufft(pk_plan_s *P);
 }  // namespace pk

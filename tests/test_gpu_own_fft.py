@@ -1,6 +1,6 @@
 """The library's own r2c transform (y and x passes, then the z transform fused
 into the bin pass) through the C ABI, against the FP64 oracle and against the
-cuFFT path on the same painted meshes.
+cuFFT path on the same painted meshes (N = 256, 512, 1024).
 
 Tolerances per bin against the unsubtracted monopole of the bin (as in the
 parity tests): 1e-4 against the oracle (FP32 form); the two GPU transforms of
@@ -70,7 +70,9 @@ def test_own_transform_matches_oracle_at_256(pk, oracle, window, interlaced, nmu
 
 @pytest.mark.parametrize("N,window,interlaced,nmu,weighted", [(512, "tsc", True, 10, False),
                                                               (512, "cic", False, 0, True),
-                                                              (256, "pcs", True, 4, True)])
+                                                              (256, "pcs", True, 4, True),
+                                                              (1024, "pcs", True, 10, False),
+                                                              (1024, "tsc", False, 0, True)])
 def test_own_and_cufft_transforms_agree(pk, N, window, interlaced, nmu, weighted):
     import synth
     L = 1000.0
@@ -122,6 +124,38 @@ def test_cross_and_projected_after_own_compute(pk, oracle):
         okp = lib["modes"] > 0
         sp = np.abs(lib["power"][okp]) + lib["shot_noise"]
         assert np.all(np.abs(got["power"] - lib["power"])[okp] <= TOL_PATHS * sp)
+
+
+def test_cross_and_projected_after_own_compute_at_1024(pk):
+    # the CTA-per-pair z pass and its in-place finish (N = 1024): cross and
+    # projected power against the cuFFT path on the same meshes
+    import synth
+    L, N = 1000.0, 1024
+    a = synth.lognormal_catalog(1_000_000, L, 256, synth.seed_for(14, 1)).numpy()
+    b = np.concatenate([a[:600000], synth.lognormal_catalog(400000, L, 256, synth.seed_for(14, 2)).numpy()])
+    cfg = pk.make_config(L, N, "tsc", interlaced=True, dk=0.01, nmu=4, batch=2)
+    out = {}
+    for own in (True, False):
+        plan = pk.pk_plan(cfg)
+        try:
+            pk.pk_use_own_fft(plan, own)
+            pk.pk_paint_many(plan, np.concatenate([a, b]), [0, len(a), len(a) + len(b)])
+            pk.pk_compute(plan)
+            ra, rb = pk.pk_result(plan, 0), pk.pk_result(plan, 1)
+            out[own] = (ra, rb, pk.pk_cross(plan, 0, 1), pk.pk_projected(plan, 1, (0, 2)))
+        finally:
+            pk.pk_destroy(plan)
+    for k in (0, 1):
+        _check_bins(out[True][k], out[False][k], out[False][k]["power"] + out[False][k]["shot_noise"], TOL_PATHS)
+    ra, rb, cross, proj = out[False]
+    ok = cross["modes"] > 0
+    scale = np.sqrt((ra["power"] + ra["shot_noise"]) * (rb["power"] + rb["shot_noise"]))
+    assert np.array_equal(out[True][2]["modes"], cross["modes"])
+    assert np.all(np.abs(out[True][2]["power"] - cross["power"])[ok] <= TOL_PATHS * scale[ok])
+    okp = proj["modes"] > 0
+    sp = np.abs(proj["power"][okp]) + proj["shot_noise"]
+    assert np.array_equal(out[True][3]["modes"], proj["modes"])
+    assert np.all(np.abs(out[True][3]["power"] - proj["power"])[okp] <= TOL_PATHS * sp)
 
 
 def test_own_transform_switch(pk):
