@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-survey", action="store_true", help="skip the survey-multipole measurement")
     ap.add_argument("--no-windows", action="store_true", help="skip the paint time per window")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 mesh form of the main workload")
+    ap.add_argument("--zeldovich-profile", action="store_true",
+                    help="two paint + compute steps of the Nmesh 2048 Zel'dovich workload only (for a launch list)")
     ap.add_argument("--survey-profile", type=int, default=0, metavar="NMESH",
                     help="only run 3 survey-multipole evaluations of a small catalog (1e5 galaxies, 1e6 randoms, "
                          "1000 Mpc/h) on an NMESH^3 mesh and print their stage times: the workload of the "
@@ -824,12 +826,41 @@ def survey_profile(nmesh):
     return 0
 
 
+def zeldovich_profile():
+    """Two paint + compute steps of the 1024^3-object Zel'dovich lattice on
+    2048^3 meshes (PCS + interlacing), the workload of `nmesh_2048`, with
+    per-stage times: the run a launch list of that configuration is taken on."""
+    import torch
+    import synth
+    import paper_1712_05834_gb300 as pk
+    pk.build()
+    torch.cuda.set_device(0)
+    L, N = 2000.0, 2048
+    pos = synth.zeldovich_lattice(1024, L, synth.seed_for(3), device="cuda")
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    stream = torch.cuda.Stream()
+    plan = pk.pk_plan(pk.make_config(L, N, "pcs", interlaced=True, dk=DK, nmu=NMU, precision="f32"), stream)
+    pk.pk_enable_timing(plan, True)
+    try:
+        for _ in range(2):
+            pk.pk_paint(plan, pos)
+            pk.pk_compute(plan)
+            pk.pk_result(plan, 0)
+            print(json.dumps(pk.pk_stage_times(plan)), flush=True)
+    finally:
+        pk.pk_destroy(plan)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.survey_profile:
         return survey_profile(args.survey_profile)
+    if args.zeldovich_profile:
+        return zeldovich_profile()
     import numpy as np
     import torch
 
