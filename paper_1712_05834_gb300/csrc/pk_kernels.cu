@@ -46,6 +46,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "pk_internal.h"
@@ -1276,7 +1277,10 @@ __global__ void k_finalize(const double *__restrict__ sums2, int nchunk, int nsu
         for (int c = 0; c < nsum; ++c) t += s0[(long long)c * f.nh + k];
         return t;
     };
-    for (int b = threadIdx.x; b < f.nk; b += blockDim.x) {
+    // bins spread over the gridDim.y blocks of the catalog (FP64 divisions are
+    // slow on this part: one block took ~30 us for 3500 bins)
+    const int t0 = blockIdx.y * blockDim.x + threadIdx.x, tstride = gridDim.y * blockDim.x;
+    for (int b = t0; b < f.nk; b += tstride) {
         double S0 = 0.0;
         if (f.twod) {
             for (int q = 0; q < f.nmu; ++q) S0 += S(b * f.nmu + q);
@@ -1298,12 +1302,12 @@ __global__ void k_finalize(const double *__restrict__ sums2, int nchunk, int nsu
         r[rl.poles + 2 * f.nk + b] = (f.poles_mask & 4u) ? p4 : nan;
     }
     if (f.twod) {
-        for (int bq = threadIdx.x; bq < f.nk * f.nmu; bq += blockDim.x) {
+        for (int bq = t0; bq < f.nk * f.nmu; bq += tstride) {
             const double cnt = (double)modes2d[bq];
             r[rl.pkmu + bq] = cnt > 0.0 ? norm * S(bq) / cnt - sub : nan;
         }
     }
-    if (threadIdx.x == 0) {
+    if (blockIdx.y == 0 && threadIdx.x == 0) {
         r[rl.shot] = shot;
         r[rl.wsum] = wsum;
         r[rl.w2sum] = w2sum;
@@ -1749,11 +1753,17 @@ cudaError_t launch_bin_reduce(const void *partial, int f64, int G, int nh, int n
     return cudaGetLastError();
 }
 
+// Blocks per catalog for k_finalize: one per 256 bins of the larger table.
+static unsigned finalize_blocks(const FinalGeom &f) {
+    const int bins = f.twod && f.nk * f.nmu > f.nk ? f.nk * f.nmu : f.nk;
+    return (unsigned)std::min(64, std::max(1, (bins + 255) / 256));
+}
+
 cudaError_t launch_finalize(const double *sums2, int G, const unsigned long long *modes1d,
                             const unsigned long long *modes2d, const double *wsums, const int *err,
                             const FinalGeom &f, int nitems, double *res, cudaStream_t st) {
     const ResultLayout rl = result_layout(f.nk, f.nmu);
-    k_finalize<<<nitems, 256, 0, st>>>(sums2, reduce_chunks(G), 1, modes1d, modes2d, wsums, err, f, rl, res, -1, -1);
+    k_finalize<<<dim3(nitems, finalize_blocks(f)), 256, 0, st>>>(sums2, reduce_chunks(G), 1, modes1d, modes2d, wsums, err, f, rl, res, -1, -1);
     return cudaGetLastError();
 }
 
@@ -1761,7 +1771,7 @@ cudaError_t launch_finalize_cross(const double *sums2, int G, const unsigned lon
                                   const unsigned long long *modes2d, const double *wsums, const int *err,
                                   const FinalGeom &f, int item_a, int item_b, double *res, cudaStream_t st) {
     const ResultLayout rl = result_layout(f.nk, f.nmu);
-    k_finalize<<<1, 256, 0, st>>>(sums2, reduce_chunks(G), 1, modes1d, modes2d, wsums, err, f, rl, res, item_a,
+    k_finalize<<<dim3(1, finalize_blocks(f)), 256, 0, st>>>(sums2, reduce_chunks(G), 1, modes1d, modes2d, wsums, err, f, rl, res, item_a,
                                   item_b);
     return cudaGetLastError();
 }
