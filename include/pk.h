@@ -269,8 +269,8 @@ pk_status pk_mesh(pk_plan_t plan, int item, int mesh, void *dst);
  * then one pass that takes the length-N/2 FFTs along z, splits the packed
  * transform into the r2c transform and bins it without writing it.  on = 0:
  * cuFFT's in-place R2C, then the bin pass.  Both give the same result within
- * FP32 rounding.  It applies to the FP32 mesh form with nmesh 256, 512, 1024
- * or 2048 and is the default at 256, 512 and 2048 (at 1024 cuFFT measured
+ * FP32 rounding.  It applies to the FP32 mesh form with nmesh 128, 192, 256,
+ * 512, 1024 or 2048 and is the default at all but 1024 (where cuFFT measured
  * faster).  After a compute with it, pk_cross
  * and pk_projected first write the r2c transform into the meshes (one extra
  * pass).  Takes effect at the next pk_compute.

@@ -428,7 +428,7 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
         PK_CUDA(P, cudaMemcpy(P->d_kedge, P->kedge.data(), sizeof(int) * (nk + 1), cudaMemcpyHostToDevice));
     }
 
-    // ---- own transform: FP32 meshes of the supported sizes (the default at 256, 512, 2048) ----
+    // ---- own transform: FP32 meshes of the supported sizes (the default at all but 1024) ----
     if (!P->f64 && own_fft_supported(P->N)) {
         std::vector<float> tw(2 * (size_t)P->N);
         own_fft_twiddles(P->N, tw.data());
@@ -781,7 +781,7 @@ pk_status pk_use_own_fft(pk_plan_t P, int on) {
     if (!P) return PK_EINVAL;
     P->err.clear();
     if (on && !P->d_tw)
-        return fail(P, PK_EINVAL, "the own transform needs the FP32 mesh form and nmesh 256, 512, 1024 or 2048");
+        return fail(P, PK_EINVAL, "the own transform needs the FP32 mesh form and nmesh 128, 192, 256, 512, 1024 or 2048");
     if (!on) {
         if (pk_status s = ensure_cufft(P); s != PK_OK) return s;
     }

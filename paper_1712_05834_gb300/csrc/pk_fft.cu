@@ -23,7 +23,8 @@
 //                    into the rows in place, for the passes that read the
 //                    transform after a compute (cross and projected power).
 // All transforms are forward (e^{-2 pi i jk/n}), unnormalized, radix-8
-// decimation in frequency with radix-4 steps where the length needs them;
+// decimation in frequency with radix-4 and radix-3 steps where the length
+// needs them (N = 2^k, 128 <= N <= 2048, and N = 192);
 // twiddles come from one table W_N^e (e < N) computed in FP64 on the host
 // (the x and y passes read W^n and W^{4n} of a butterfly from it and form
 // its other twiddles as products, a few ulp each).
@@ -60,6 +61,16 @@ __device__ __forceinline__ void dft<4>(float2 *v) {
     v[3] = c_sub(b, d);
 }
 
+template <>
+__device__ __forceinline__ void dft<3>(float2 *v) {
+    const float h = 0.86602540378443865f;                      // sqrt(3) / 2
+    const float2 s = c_add(v[1], v[2]), d = c_sub(v[1], v[2]);
+    const float2 m = make_float2(v[0].x - 0.5f * s.x, v[0].y - 0.5f * s.y);
+    v[0] = c_add(v[0], s);
+    v[1] = make_float2(m.x + h * d.y, m.y - h * d.x);          // W_3 = -1/2 - i sqrt(3)/2
+    v[2] = make_float2(m.x - h * d.y, m.y + h * d.x);
+}
+
 // Split into the even and odd outputs: X[2k] = DFT4(v[j] + v[j+4]),
 // X[2k+1] = DFT4((v[j] - v[j+4]) W_8^j).
 template <>
@@ -83,9 +94,12 @@ __device__ __forceinline__ void dft<8>(float2 *v) {
     }
 }
 
-// Radix of the decimation-in-frequency step over blocks of S points (S a
-// power of two >= 4): 8, with 4 for the blocks of 16 and 4 points.
-__host__ __device__ constexpr int radix_of(int S) { return (S == 4 || S == 16) ? 4 : 8; }
+// Radix of the decimation-in-frequency step over blocks of S points: 8, with
+// 4 for the blocks of 16, 12 and 4 points and 3 for a block of 3 (lengths
+// 2^k >= 4 and 3 * 2^k: 192 runs 8, 8, 3 and 96 runs 8, 4, 3).
+__host__ __device__ constexpr int radix_of(int S) {
+    return S == 3 ? 3 : (S == 4 || S == 12 || S == 16) ? 4 : 8;
+}
 
 // Radix order of the z FFTs: as radix_of, but 4 for the blocks of 32 (a
 // length-256 transform runs 8, 4, 8).
@@ -120,8 +134,9 @@ __device__ __forceinline__ int dif_freq(int p) {
 template <int LEN>
 struct AxisCfg {
     static constexpr int NB = LEN >= 2048 ? 8 : 16;        // columns per tile
-    static constexpr int T = LEN >= 1024 ? 1024 : 512;     // threads per CTA
-    static constexpr int MINB = LEN >= 1024 ? 1 : 2;       // CTAs per SM
+    // threads per CTA (for 192 lines: 8 butterfly groups divide 24 and 64)
+    static constexpr int T = LEN >= 1024 ? 1024 : (LEN >= 256 ? 512 : (LEN == 192 ? 128 : 256));
+    static constexpr int MINB = LEN >= 1024 ? 1 : (LEN >= 256 ? 2 : (LEN == 192 ? 8 : 4));   // CTAs per SM
 };
 
 template <int LEN, int NB, int S, bool FIRST>
@@ -169,9 +184,12 @@ __device__ __forceinline__ void axis_step(float2 *buf, float2 *g, long long astr
                     ww[5] = c_mul(ww[4], ww[1]);
                     ww[6] = c_mul(ww[4], ww[2]);
                     ww[7] = c_mul(ww[4], ww[3]);
-                } else {
+                } else if constexpr (R == 4) {
                     ww[2] = tw[2 * n * E];
                     ww[3] = c_mul(ww[2], ww[1]);
+                } else {
+#pragma unroll
+                    for (int k = 2; k < R; ++k) ww[k] = tw[k * n * E];
                 }
 #pragma unroll
                 for (int k = 1; k < R; ++k) v[s][k] = c_mul(v[s][k], ww[k]);
@@ -232,7 +250,9 @@ __device__ __forceinline__ int zslot(int p) { return p ^ ((p >> 2) & 15); }
 // time), by the whole CTA above (its four rows of M complex are 16 or 32 KB).
 template <int M>
 struct ZRows {
-    static constexpr int RS = M + 2;              // slots per row: positions 0..M, even
+    // slots per row: positions 0..M, even (zslot(M) = M for M = 2^k >= 64;
+    // up to M + 15 otherwise)
+    static constexpr int RS = (M & (M - 1)) == 0 ? M + 2 : M + 16;
     static constexpr int WPB = 8;                 // warps per CTA
     static constexpr int NT = M >= 512 ? 256 : 32;   // threads per pair
     static constexpr int PPC = 256 / NT;          // pairs in flight per CTA
@@ -431,7 +451,7 @@ __device__ __forceinline__ void bin_pair(const float2 *rows, int i, int j, int p
                 const int2 e = sedge[b];
                 b += (int)(m >= e.y) - (int)(m < e.x);
             }
-            const int sl = zslot(l), la = zslot(l & (M - 1)), lb = zslot((M - l) & (M - 1));
+            const int sl = zslot(l), la = zslot(l == M ? 0 : l), lb = zslot(l == 0 ? 0 : M - l);
             const float2 w = swl[sl];
             float2 dA = split2(a1[la], b1[lb], w);
             float2 dB = split2(b1[la], a1[lb], w);
@@ -530,7 +550,7 @@ k_zbin(const float2 *__restrict__ mesh, long long item_stride_c, long long mesh_
         int llo = g.mlo > r2 ? isqrt_floor_z(g.mlo - r2 - 1) + 1 : 0;
         if (r2 == 0 && llo == 0) llo = 1;
         if (llo >= lhi) continue;
-        const int pi = (N - i) & (N - 1), pj = (N - j) & (N - 1);
+        const int pi = i == 0 ? 0 : N - i, pj = j == 0 ? 0 : N - j;
         const long long offA = ((long long)i * N + j) * Nh, offB = ((long long)pi * N + pj) * Nh;
         pair_sync<NT>();    // the previous pair's bin reads are done
         zfft_step<M, NR, M, true, NT>(rows, m1, m2, offA, offB, ztw, lane);
@@ -563,7 +583,7 @@ k_zfinish(float2 *__restrict__ mesh, long long item_stride_c, long long mesh_str
     for (int p = blockIdx.x * PPC + grp; p < npairs; p += gridDim.x * PPC) {
         int i, j;
         pair_rows(p, N, &i, &j);
-        const int pi = (N - i) & (N - 1), pj = (N - j) & (N - 1);
+        const int pi = i == 0 ? 0 : N - i, pj = j == 0 ? 0 : N - j;
         const long long offA = ((long long)i * N + j) * Nh, offB = ((long long)pi * N + pj) * Nh;
         pair_sync<NT>();
         zfft_step<M, NR, M, true, NT>(rows, m1, m2, offA, offB, ztw, lane);
@@ -575,7 +595,7 @@ k_zfinish(float2 *__restrict__ mesh, long long item_stride_c, long long mesh_str
             float2 *dst = q ? m2 : m1;
             const float2 *ra = rows + (2 * q) * RS, *rb = ra + RS;
             for (int l = lane; l < Nh; l += NT) {
-                const int sl = zslot(l), la = zslot(l & (M - 1)), lb = zslot((M - l) & (M - 1));
+                const int sl = zslot(l), la = zslot(l == M ? 0 : l), lb = zslot(l == 0 ? 0 : M - l);
                 const float2 w = swl[sl];
                 const float2 dA = split2(ra[la], rb[lb], w);
                 dst[offA + l] = make_float2(0.5f * dA.x, 0.5f * dA.y);
@@ -645,13 +665,14 @@ cudaError_t zfinish_inst(void *mesh, long long is, long long ms, int nitems, int
 
 }  // namespace
 
-bool own_fft_supported(int N) { return N == 256 || N == 512 || N == 1024 || N == 2048; }
+bool own_fft_supported(int N) { return N == 128 || N == 192 || N == 256 || N == 512 || N == 1024 || N == 2048; }
 
-// Measured on a GB300 (FFT + bin): 512^3 1.25 against 1.84 ms with cuFFT,
+// Measured on a GB300 (FFT + bin): 32 catalogs of 128^3 0.40 against 0.56 ms
+// with cuFFT, 24 of 192^3 1.07 against 1.35 ms, 512^3 1.25 against 1.84 ms,
 // 2048^3 121 against 234 ms; at 1024^3 13.4 against 12.7 ms (the CTA-per-pair
-// z pass is latency-bound at 16 warps per SM), so 1024 keeps cuFFT unless
-// the caller asks for the own transform.
-bool own_fft_default(int N) { return N == 256 || N == 512 || N == 2048; }
+// z pass is latency-bound at 16 warps per SM), so 1024 keeps cuFFT unless the
+// caller asks for the own transform.
+bool own_fft_default(int N) { return N == 128 || N == 192 || N == 256 || N == 512 || N == 2048; }
 
 void own_fft_twiddles(int N, float *tw) {
     for (int e = 0; e < N; ++e) {
@@ -670,6 +691,8 @@ cudaError_t launch_fft_xy(void *mesh, int nmesh, long long mesh_c, int N, const 
     float2 *m = reinterpret_cast<float2 *>(mesh);
     const float2 *t = reinterpret_cast<const float2 *>(tw);
     switch (N) {
+    case 128: return axis_inst<128>(m, nmesh, mesh_c, t, st);
+    case 192: return axis_inst<192>(m, nmesh, mesh_c, t, st);
     case 256: return axis_inst<256>(m, nmesh, mesh_c, t, st);
     case 512: return axis_inst<512>(m, nmesh, mesh_c, t, st);
     case 1024: return axis_inst<1024>(m, nmesh, mesh_c, t, st);
@@ -680,6 +703,8 @@ cudaError_t launch_fft_xy(void *mesh, int nmesh, long long mesh_c, int N, const 
 
 size_t zbin_smem_bytes(const BinGeom &g, int interlaced) {
     switch (g.N) {
+    case 128: return interlaced ? ZSmem<64, 4>::bytes(g) : ZSmem<64, 2>::bytes(g);
+    case 192: return interlaced ? ZSmem<96, 4>::bytes(g) : ZSmem<96, 2>::bytes(g);
     case 256: return interlaced ? ZSmem<128, 4>::bytes(g) : ZSmem<128, 2>::bytes(g);
     case 512: return interlaced ? ZSmem<256, 4>::bytes(g) : ZSmem<256, 2>::bytes(g);
     case 1024: return interlaced ? ZSmem<512, 4>::bytes(g) : ZSmem<512, 2>::bytes(g);
@@ -697,7 +722,11 @@ int zbin_ctas_per_sm(const BinGeom &g, int interlaced) {
     threads = 32 * ZRows<M>::WPB;                                                                           \
     kern = interlaced ? reinterpret_cast<const void *>(k_zbin<true, true, true, true, M>)                   \
                       : reinterpret_cast<const void *>(k_zbin<false, true, true, true, M>);
-    if (g.N == 256) {
+    if (g.N == 128) {
+        PK_ZK(64)
+    } else if (g.N == 192) {
+        PK_ZK(96)
+    } else if (g.N == 256) {
         PK_ZK(128)
     } else if (g.N == 512) {
         PK_ZK(256)
@@ -723,6 +752,12 @@ cudaError_t launch_zbin(const void *mesh, int interlaced, long long item_stride_
                         int nitems, int ctas_per_item, const BinGeom &g, const void *cw, const void *ph,
                         const void *tw, const int *kedge, void *partial, cudaStream_t st) {
     switch (g.N) {
+    case 128:
+        return zbin_dispatch<64>(mesh, interlaced, item_stride_c, mesh_stride_c, nitems, ctas_per_item, g, cw,
+                                 ph, tw, kedge, partial, st);
+    case 192:
+        return zbin_dispatch<96>(mesh, interlaced, item_stride_c, mesh_stride_c, nitems, ctas_per_item, g, cw,
+                                 ph, tw, kedge, partial, st);
     case 256:
         return zbin_dispatch<128>(mesh, interlaced, item_stride_c, mesh_stride_c, nitems, ctas_per_item, g, cw,
                                   ph, tw, kedge, partial, st);
@@ -742,6 +777,12 @@ cudaError_t launch_zbin(const void *mesh, int interlaced, long long item_stride_
 cudaError_t launch_zfinish(void *mesh, int interlaced, long long item_stride_c, long long mesh_stride_c,
                            int nitems, int N, const void *tw, int nsm, cudaStream_t st) {
     switch (N) {
+    case 128:
+        return interlaced ? zfinish_inst<64, 4>(mesh, item_stride_c, mesh_stride_c, nitems, nsm, tw, st)
+                          : zfinish_inst<64, 2>(mesh, item_stride_c, mesh_stride_c, nitems, nsm, tw, st);
+    case 192:
+        return interlaced ? zfinish_inst<96, 4>(mesh, item_stride_c, mesh_stride_c, nitems, nsm, tw, st)
+                          : zfinish_inst<96, 2>(mesh, item_stride_c, mesh_stride_c, nitems, nsm, tw, st);
     case 256:
         return interlaced ? zfinish_inst<128, 4>(mesh, item_stride_c, mesh_stride_c, nitems, nsm, tw, st)
                           : zfinish_inst<128, 2>(mesh, item_stride_c, mesh_stride_c, nitems, nsm, tw, st);

@@ -121,7 +121,7 @@ cudaError_t launch_plane_bin(const void *m1, const void *m2, int f64, int N, int
                              const void *ph, const int *kedge, int nk, double kF, double *sums, int nsm,
                              cudaStream_t st);
 
-// ---- own FFT path (pk_fft.cu), FP32 meshes with N in {256, 512, 1024, 2048} ----
+// ---- own FFT path (pk_fft.cu), FP32 meshes with N in {128, 192, 256, 512, 1024, 2048} ----
 // The meshes' z rows are read as N/2 complex values (packed real pairs).
 bool own_fft_supported(int N);
 bool own_fft_default(int N);                      // pk_compute uses it unless told otherwise

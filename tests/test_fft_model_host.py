@@ -1,8 +1,9 @@
 """The decomposition behind the library's own r2c transform, modelled on the
 CPU and checked against numpy's FFT (no GPU):
 
-* the radix schedules of the x / y passes (radix 8, radix 4 for blocks of 16
-  and 4) and of the z FFTs (also radix 4 for blocks of 32), with the
+* the radix schedules of the x / y passes (radix 8, radix 4 for blocks of 16,
+  12 and 4, radix 3 for a block of 3) and of the z FFTs (also radix 4 for
+  blocks of 32), with the
   decimation-in-frequency twiddles W_S^{nk} and the digit-reversed output
   positions the kernels write back in natural order;
 * a real z row d read as N/2 complex values d[2n] + i d[2n+1], transformed
@@ -16,7 +17,7 @@ import pytest
 
 
 def radix_axis(S):
-    return 4 if S in (4, 16) else 8
+    return 3 if S == 3 else (4 if S in (4, 12, 16) else 8)
 
 
 def radix_z(S):
@@ -58,14 +59,18 @@ def dif_fft(x, radix):
     return out
 
 
-@pytest.mark.parametrize("L", [64, 128, 256, 512, 1024, 2048])
+@pytest.mark.parametrize("L", [64, 128, 192, 256, 512, 1024, 2048])
 def test_axis_schedule_is_the_dft(L):
     x = np.random.default_rng(L).standard_normal(L) + 1j * np.random.default_rng(L + 1).standard_normal(L)
     np.testing.assert_allclose(dif_fft(x, radix_axis), np.fft.fft(x), rtol=0, atol=1e-10 * np.sqrt(L))
 
 
-@pytest.mark.parametrize("M", [64, 128, 256, 512, 1024])
+@pytest.mark.parametrize("M", [64, 96, 128, 256, 512, 1024])
 def test_z_schedule_is_the_dft(M):
+    # also the row slots: position p at p ^ ((p >> 2) & 15), a bijection on
+    # [0, M] below M + 16 (below M + 2 for powers of two)
+    slots = [p ^ ((p >> 2) & 15) for p in range(M + 1)]
+    assert len(set(slots)) == M + 1 and max(slots) < (M + 2 if (M & (M - 1)) == 0 else M + 16)
     x = np.random.default_rng(M).standard_normal(M) + 1j * np.random.default_rng(M + 7).standard_normal(M)
     np.testing.assert_allclose(dif_fft(x, radix_z), np.fft.fft(x), rtol=0, atol=1e-10 * np.sqrt(M))
 
@@ -83,7 +88,7 @@ def split2(u, v, w):
     return (u + np.conj(v)) - 1j * w * (u - np.conj(v))
 
 
-@pytest.mark.parametrize("N", [8, 16, 32])
+@pytest.mark.parametrize("N", [8, 16, 24, 32])
 def test_packed_rows_and_pair_split_give_rfftn(N):
     M = N // 2
     d = np.random.default_rng(N).standard_normal((N, N, N))

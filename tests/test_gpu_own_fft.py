@@ -1,6 +1,6 @@
 """The library's own r2c transform (y and x passes, then the z transform fused
 into the bin pass) through the C ABI, against the FP64 oracle and against the
-cuFFT path on the same painted meshes (N = 256, 512, 1024).
+cuFFT path on the same painted meshes (N = 128, 192, 256, 512, 1024).
 
 Tolerances per bin against the unsubtracted monopole of the bin (as in the
 parity tests): 1e-4 against the oracle (FP32 form); the two GPU transforms of
@@ -71,6 +71,10 @@ def test_own_transform_matches_oracle_at_256(pk, oracle, window, interlaced, nmu
 @pytest.mark.parametrize("N,window,interlaced,nmu,weighted", [(512, "tsc", True, 10, False),
                                                               (512, "cic", False, 0, True),
                                                               (256, "pcs", True, 4, True),
+                                                              (128, "cic", False, 0, False),
+                                                              (128, "tsc", True, 5, True),
+                                                              (192, "cic", False, 0, False),
+                                                              (192, "tsc", True, 4, True),
                                                               (1024, "pcs", True, 10, False),
                                                               (1024, "tsc", False, 0, True)])
 def test_own_and_cufft_transforms_agree(pk, N, window, interlaced, nmu, weighted):
