@@ -1,4 +1,5 @@
-"""Bit-exact check of the bin kernel's own mode-to-bin assignment.
+"""Bit-exact check of the bin kernels' own mode-to-bin assignment (k_bin and the
+own transform's fused z + bin pass).
 
 The mode counts that pk_result reports come from the plan-time geometry pass;
 the bin kernel itself places every mode in a k bin from an FP32 estimate plus
@@ -102,3 +103,45 @@ def test_bin_kernel_near_the_k_resolution_limit(pk, oracle, N, L):
     assert nk == c1.shape[0] and 7990 <= nk <= 8000
     assert np.array_equal(got, c1)
     assert np.count_nonzero(c1) > 10
+
+
+# The own transform's fused z + bin pass has no transform to inject, so its
+# placement is checked through the plan path with a painted delta: one object
+# of weight 1 exactly on node (0, 0, 0), CIC, not interlaced, uncompensated,
+# no shot-noise subtraction.  Its mesh is 1 at cell 0 and 0 elsewhere, every
+# step of the own transform is then exact in FP32 (sums of one 1 and zeros,
+# twiddles W^0 = 1), the split gives 2 D = 2 exactly and every mode's power is
+# L^3 * 1.  Each bin's sum is its own h-weighted mode count (exact in the FP32
+# partials), so P(k) and P(k, mu) equal L^3 exactly iff the kernel placed
+# every mode where the plan's exact geometry counted it.  L = 512 makes L^3 a
+# power of two, so the FP64 normalization is exact too.
+@pytest.mark.parametrize("N,dk_kf,nmu,kmin_kf,kmax_kn,own", [
+    (128, 1.5, 7, 0.0, None, True),
+    (128, 1.0, 0, 0.37, 0.9, True),
+    (192, 1.3, 5, 0.0, None, True),        # radix-3 steps
+    (256, 0.9, 10, 2.1, 0.8, True),
+    (512, 1.226, 10, 0.0, None, True),
+    (1024, 1.7, 3, 0.0, None, True),       # CTA-per-pair z pass (opt-in size)
+    (2048, 2.3, 64, 0.0, None, True),      # CTA per pair, 64-bit mu rule
+])
+def test_own_transform_places_every_mode_in_its_exact_bin(pk, N, dk_kf, nmu, kmin_kf, kmax_kn, own):
+    L = 512.0
+    kF, kN = 2.0 * math.pi / L, math.pi * N / L
+    cfg = pk.make_config(L, N, "cic", interlaced=False, compensated=False, dk=dk_kf * kF, nmu=nmu,
+                         kmin=kmin_kf * kF, kmax=None if kmax_kn is None else kmax_kn * kN, subtract_shot=False)
+    plan = pk.pk_plan(cfg)
+    try:
+        pk.pk_use_own_fft(plan, own)
+        pk.pk_paint(plan, np.zeros((1, 3), np.float32))
+        pk.pk_compute(plan)
+        r = pk.pk_result(plan, 0)
+    finally:
+        pk.pk_destroy(plan)
+    ok = r["modes"] > 0
+    assert np.count_nonzero(ok) > 3
+    assert np.all(r["power"][ok] == L ** 3), np.unique(r["power"][ok] / L ** 3)
+    assert np.all(np.isnan(r["power"][~ok]))
+    if nmu > 0:
+        ok2 = r["modes2d"] > 0
+        assert np.all(r["power2d"][ok2] == L ** 3), np.unique(r["power2d"][ok2] / L ** 3)
+        assert np.array_equal(r["modes2d"].sum(axis=1), r["modes"])
