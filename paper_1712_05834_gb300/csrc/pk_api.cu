@@ -67,7 +67,7 @@ void free_plan(pk_plan_s *p) {
     if (!p) return;
     cudaStreamSynchronize(p->st);
     for (cufftHandle h : p->fft) cufftDestroy(h);
-    void *dev[] = {p->mesh, p->d_count, p->d_off, p->d_scan_tmp, p->d_rank, p->d_sorted,
+    void *dev[] = {p->mesh, p->d_count, p->d_off, p->d_scan_tmp, p->d_sorted,
                    p->d_stage, p->d_item_off, p->d_wsums, p->d_wmax, p->d_cw, p->d_ph,
                    p->d_kedge, p->d_partial, p->d_sums2, p->d_res, p->d_modes1d, p->d_modes2d,
                    p->d_err, p->d_acc, p->fft_work, p->d_xres, p->d_proj, p->d_tw};
@@ -398,7 +398,6 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
         PK_CUDA(P, cudaMemset(P->d_acc, 0, acc_bytes));
     } else if (c.capacity > 0) {
         PK_CUDA(P, dev_alloc(&P->d_sorted, sizeof(float4) * (size_t)c.capacity));
-        PK_CUDA(P, dev_alloc(&P->d_rank, sizeof(uint32_t) * (size_t)c.capacity));
         P->sorted_cap = c.capacity;
     }
     PK_CUDA(P, dev_alloc(&P->d_modes1d, sizeof(unsigned long long) * nk));
@@ -622,12 +621,9 @@ static pk_status paint_impl(pk_plan_s *P, const void *pos, int dtype, const floa
     if (ntot > P->sorted_cap) {                 // grow the key-ordered copy (rare)
         PK_CUDA(P, cudaStreamSynchronize(st));
         if (P->d_sorted) cudaFree(P->d_sorted);
-        if (P->d_rank) cudaFree(P->d_rank);
         P->d_sorted = nullptr;
-        P->d_rank = nullptr;
         P->sorted_cap = 0;
         PK_CUDA(P, cudaMalloc(reinterpret_cast<void **>(&P->d_sorted), sizeof(float4) * (size_t)ntot));
-        PK_CUDA(P, cudaMalloc(reinterpret_cast<void **>(&P->d_rank), sizeof(uint32_t) * (size_t)ntot));
         P->sorted_cap = ntot;
     }
     const long long nkeys = (long long)nitems * P->nkeys;
@@ -641,10 +637,10 @@ static pk_status paint_impl(pk_plan_s *P, const void *pos, int dtype, const floa
         PK_CUDA(P, cudaMemsetAsync(P->d_wmax, 0, sizeof(unsigned) * nitems, st));
     }
     PK_CUDA(P, launch_sort_count(dpos, dtype, dw, dv, P->d_item_off, nitems, max_n, P->pg, P->d_count,
-                                 P->d_rank, P->d_wsums, P->d_wmax, st));
+                                 P->d_wsums, P->d_wmax, st));
     PK_CUDA(P, launch_scan(P->d_count, nkeys, P->d_off, P->d_scan_tmp, &launches, st));
     PK_CUDA(P, launch_sort_scatter(dpos, dtype, dw, dv, P->d_item_off, nitems, max_n, P->pg, P->d_off,
-                                   P->d_rank, P->d_sorted, P->d_err, st));
+                                   P->d_count, P->d_sorted, P->d_err, st));
     if (tm) PK_CUDA(P, cudaEventRecord(P->tev[1], st));
     const int unit_weights = dw == nullptr && dv == nullptr && dtype != PK_F32X4;
     PK_CUDA(P, launch_paint_tiles(P->d_sorted, P->d_off, nitems, P->pg, P->p, P->nm, P->S, P->f64,

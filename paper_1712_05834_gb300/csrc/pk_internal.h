@@ -66,14 +66,14 @@ cudaError_t launch_upload_i64(int64_t *dst, const int64_t *src, int n, int *laun
 // each object deposits W V and the sums keep sum W, sum (W V)^2, sum |W V|.
 cudaError_t launch_sort_count(const void *pos, int dtype, const float *w, const float *vals,
                               const int64_t *item_off, int nitems, int64_t max_n, const PaintGeom &g,
-                              uint32_t *count, uint32_t *rank, double *wsums, unsigned *wmax, cudaStream_t st);
+                              uint32_t *count, double *wsums, unsigned *wmax, cudaStream_t st);
 cudaError_t launch_scan(const uint32_t *in, int64_t n, uint32_t *out, uint32_t *tmp, int *launches,
                         cudaStream_t st);
 cudaError_t launch_scan64(const unsigned long long *in, int64_t n, unsigned long long *out,
                           unsigned long long *tmp, int *launches, cudaStream_t st);
 cudaError_t launch_sort_scatter(const void *pos, int dtype, const float *w, const float *vals,
                                 const int64_t *item_off, int nitems, int64_t max_n, const PaintGeom &g,
-                                const uint32_t *off, const uint32_t *rank, float4 *sorted, int *err,
+                                const uint32_t *off, uint32_t *count, float4 *sorted, int *err,
                                 cudaStream_t st);
 cudaError_t launch_paint_tiles(const float4 *sorted, const uint32_t *off, int nitems,
                                const PaintGeom &g, int window, int nmesh, int S, int f64,

@@ -4,12 +4,15 @@
 // interlacing with a second mesh shifted by half a cell):
 //   k_sort_count    wrap each object into the box, find its home tile (T^3
 //                   cells) and its boundary class (per axis: near the low
-//                   face, interior, near the high face -- 27 classes), count
-//                   objects per (tile, class) key and record each object's
-//                   rank inside its key; sum w, w^2, |w| and max |w|.
+//                   face, interior, near the high face -- 27 classes) and
+//                   count objects per (tile, class) key (reductions whose
+//                   result nobody waits for); sum w, w^2, |w| and max |w|.
 //   k_scan_*        exclusive scan of the key counts (uint32).
 //   k_sort_scatter  write one float4 (home-tile-local x, y, z, w) per object
-//                   at offset[key] + rank: no atomics, no copies, size n.
+//                   at offset[key] + (its key's count, decremented): the
+//                   order inside a key is whatever order the decrements are
+//                   served in, which the paint's integer deposits do not
+//                   see; the counts end at zero.  No per-object rank array.
 //   k_paint_tiles   one CTA per tile: gather the tile's own objects and the
 //                   boundary classes of its 26 neighbours whose window reaches
 //                   into it, deposit B-spline weights into shared memory as
@@ -214,12 +217,20 @@ __device__ __forceinline__ void flush_wsums(double sw, double sw2, double swa, f
     }
 }
 
-// Tile sort, pass 1: key counts and ranks, plus the weight sums.
+// Key of an object: (catalog, home tile, boundary class).
+template <typename R>
+__device__ __forceinline__ int64_t sort_key(const Obj<R> &o, const PaintGeom &g, int64_t kbase, int *t3) {
+    int cls;
+    home_key<R>(o, g, t3, &cls);
+    return kbase + (((int64_t)t3[0] * g.ntx + t3[1]) * g.ntx + t3[2]) * kClasses + cls;
+}
+
+// Tile sort, pass 1: key counts, plus the weight sums.
 template <int DT, bool WEIGHTED>
 __global__ void __launch_bounds__(kCountThreads)
 k_sort_count(const void *__restrict__ pos, const float *__restrict__ w, const float *__restrict__ vals,
              const int64_t *__restrict__ item_off, PaintGeom g, uint32_t *__restrict__ count,
-             uint32_t *__restrict__ rank, double *__restrict__ wsums, unsigned *__restrict__ wmax) {
+             double *__restrict__ wsums, unsigned *__restrict__ wmax) {
     using R = typename PosReal<DT>::type;
     const int item = blockIdx.y;
     const int64_t beg = item_off[item], end = item_off[item + 1];
@@ -229,10 +240,8 @@ k_sort_count(const void *__restrict__ pos, const float *__restrict__ w, const fl
     for (int64_t i = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end;
          i += (int64_t)gridDim.x * blockDim.x) {
         const Obj<R> o = load_obj<DT>(pos, w, vals, i, g);
-        int t3[3], cls;
-        home_key<R>(o, g, t3, &cls);
-        const int64_t key = kbase + (((int64_t)t3[0] * g.ntx + t3[1]) * g.ntx + t3[2]) * kClasses + cls;
-        rank[i] = atomicAdd(count + key, 1u);
+        int t3[3];
+        atomicAdd(count + sort_key<R>(o, g, kbase, t3), 1u);   // result unused: a reduction
         if (WEIGHTED) {
             const double ad = (double)o.a;
             sw += (double)o.w;
@@ -244,11 +253,16 @@ k_sort_count(const void *__restrict__ pos, const float *__restrict__ w, const fl
     flush_wsums(sw, sw2, swa, mw, WEIGHTED, item, end - beg, wsums, wmax);
 }
 
+// Tile sort, pass 2: each object takes the last free slot of its key's range
+// (the key's count, decremented: objects of the key not yet placed, this one
+// included).  Measured: both passes are bound by the L2's atomic rate, not by
+// its latency (two, four or eight objects per thread with every load and
+// atomic issued before the first use ran 4 %, 10 % and 23 % slower).
 template <int DT>
 __global__ void __launch_bounds__(kCountThreads)
 k_sort_scatter(const void *__restrict__ pos, const float *__restrict__ w, const float *__restrict__ vals,
                const int64_t *__restrict__ item_off, PaintGeom g, const uint32_t *__restrict__ off,
-               const uint32_t *__restrict__ rank, float4 *__restrict__ sorted, int *__restrict__ err) {
+               uint32_t *__restrict__ count, float4 *__restrict__ sorted, int *__restrict__ err) {
     using R = typename PosReal<DT>::type;
     const int item = blockIdx.y;
     const int64_t beg = item_off[item], end = item_off[item + 1];
@@ -256,17 +270,17 @@ k_sort_scatter(const void *__restrict__ pos, const float *__restrict__ w, const 
     for (int64_t i = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < end;
          i += (int64_t)gridDim.x * blockDim.x) {
         const Obj<R> o = load_obj<DT>(pos, w, vals, i, g);
-        int t3[3], cls;
-        home_key<R>(o, g, t3, &cls);
-        const int64_t key = kbase + (((int64_t)t3[0] * g.ntx + t3[1]) * g.ntx + t3[2]) * kClasses + cls;
-        const uint32_t dst = off[key] + rank[i];
-        if (dst >= off[key + 1]) {              // count and scatter disagree: never write
+        int t3[3];
+        const int64_t key = sort_key<R>(o, g, kbase, t3);
+        const uint32_t left = atomicSub(count + key, 1u);
+        const uint32_t first = off[key];
+        if (left == 0 || left > off[key + 1] - first) {   // count and scatter disagree: never write
             atomicOr(err, 2);
             continue;
         }
-        sorted[dst] = make_float4((float)(o.s[0] - (R)(t3[0] * g.T)) + o.e[0],
-                                  (float)(o.s[1] - (R)(t3[1] * g.T)) + o.e[1],
-                                  (float)(o.s[2] - (R)(t3[2] * g.T)) + o.e[2], o.a);
+        sorted[first + left - 1] = make_float4((float)(o.s[0] - (R)(t3[0] * g.T)) + o.e[0],
+                                               (float)(o.s[1] - (R)(t3[1] * g.T)) + o.e[1],
+                                               (float)(o.s[2] - (R)(t3[2] * g.T)) + o.e[2], o.a);
     }
 }
 
@@ -1451,12 +1465,12 @@ int paint_classes() { return kClasses; }
 
 cudaError_t launch_sort_count(const void *pos, int dtype, const float *w, const float *vals,
                               const int64_t *item_off, int nitems, int64_t max_n, const PaintGeom &g,
-                              uint32_t *count, uint32_t *rank, double *wsums, unsigned *wmax, cudaStream_t st) {
+                              uint32_t *count, double *wsums, unsigned *wmax, cudaStream_t st) {
     dim3 grid(grid_for(max_n, kCountThreads, 1u << 20), nitems);
     const bool weighted = w != nullptr || vals != nullptr || dtype == PK_F32X4;
 #define PK_COUNT(DT)                                                                                    \
-    if (weighted) k_sort_count<DT, true><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, count, rank, wsums, wmax); \
-    else k_sort_count<DT, false><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, count, rank, wsums, wmax);
+    if (weighted) k_sort_count<DT, true><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, count, wsums, wmax); \
+    else k_sort_count<DT, false><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, count, wsums, wmax);
     switch (dtype) {
     case PK_F32: PK_COUNT(PK_F32) break;
     case PK_F64: PK_COUNT(PK_F64) break;
@@ -1468,13 +1482,13 @@ cudaError_t launch_sort_count(const void *pos, int dtype, const float *w, const 
 
 cudaError_t launch_sort_scatter(const void *pos, int dtype, const float *w, const float *vals,
                                 const int64_t *item_off, int nitems, int64_t max_n, const PaintGeom &g,
-                                const uint32_t *off, const uint32_t *rank, float4 *sorted, int *err,
+                                const uint32_t *off, uint32_t *count, float4 *sorted, int *err,
                                 cudaStream_t st) {
     dim3 grid(grid_for(max_n, kCountThreads, 1u << 20), nitems);
     switch (dtype) {
-    case PK_F32: k_sort_scatter<PK_F32><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, off, rank, sorted, err); break;
-    case PK_F64: k_sort_scatter<PK_F64><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, off, rank, sorted, err); break;
-    default: k_sort_scatter<PK_F32X4><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, off, rank, sorted, err); break;
+    case PK_F32: k_sort_scatter<PK_F32><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, off, count, sorted, err); break;
+    case PK_F64: k_sort_scatter<PK_F64><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, off, count, sorted, err); break;
+    default: k_sort_scatter<PK_F32X4><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, off, count, sorted, err); break;
     }
     return cudaGetLastError();
 }

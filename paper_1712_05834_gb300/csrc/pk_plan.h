@@ -41,7 +41,6 @@ struct pk_plan_s {
     uint32_t *d_count = nullptr;     // objects per (tile, class) key
     uint32_t *d_off = nullptr;       // exclusive scan of d_count (+ total)
     uint32_t *d_scan_tmp = nullptr;
-    uint32_t *d_rank = nullptr;      // rank of each object inside its key
     float4 *d_sorted = nullptr;      // objects in key order, home-tile-local xyz + w
     int64_t sorted_cap = 0;
     long long nkeys = 0;             // keys per catalog

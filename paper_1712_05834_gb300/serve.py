@@ -67,7 +67,7 @@ def slot_bytes(nmesh: int, interlaced: bool, precision: str, batch: int, capacit
     if variant == "atomic":
         paint = batch * nm * nmesh ** 3 * 8
     else:
-        paint = capacity * 20 + 2 * batch * (nmesh // max(tile, 1)) ** 3 * 27 * 4
+        paint = capacity * 16 + 2 * batch * (nmesh // max(tile, 1)) ** 3 * 27 * 4
     staging = capacity * 16
     return int(mesh + work + paint + staging + (8 << 20))
 

@@ -82,6 +82,20 @@ def _displacement(gk, box_size: float, axis: int):
     return torch.fft.irfftn(psi_k, s=(ng, ng, ng))
 
 
+def _cell_cdf(rho, ngrid: int):
+    """Running sum of the cell weights in cell order.  On the CPU a plain
+    cumsum (sequential, the same every run).  On a GPU a 1-D cumsum is a
+    single-pass scan whose floating-point summation order depends on the
+    timing of its blocks, so two processes could draw different cells for
+    the same seed; there each z row is summed on its own (one row per
+    thread block, a fixed order) and the row totals are summed on the host."""
+    if rho.device.type == "cpu":
+        return torch.cumsum(rho, 0)
+    rows = torch.cumsum(rho.reshape(ngrid * ngrid, ngrid), 1)
+    start = torch.cumsum(rows[:, -1].cpu(), 0) - rows[:, -1].cpu()
+    return (rows + start.to(rho.device)[:, None]).reshape(-1)
+
+
 def lognormal_catalog(n: int, box_size: float, ngrid: int, seed: int, slope: float = -1.5,
                       variance: float = 1.0, f_rsd: float = 0.75, device="cpu",
                       dtype=torch.float32):
@@ -98,7 +112,7 @@ def lognormal_catalog(n: int, box_size: float, ngrid: int, seed: int, slope: flo
     sig2 = float(g.double().var())
     rho = torch.exp(g.double() - 0.5 * sig2).reshape(-1)
     del g
-    cdf = torch.cumsum(rho, 0)
+    cdf = _cell_cdf(rho, ngrid)
     del rho
     gen = torch.Generator(device=device)
     gen.manual_seed(int(seed) + 1)
