@@ -17,7 +17,11 @@ whose batch holds all of its catalogs, back to back in one device buffer:
 The whole sequence for all classes is captured once into a CUDA graph on the
 runner's stream and replayed per evaluation; the graph re-reads the position
 buffers in place, so refilling them with new mocks and replaying evaluates the
-new mocks.  The autotuner picks, per class, the paint variant (tile sort or
+new mocks.  Classes are independent: with ``streams`` > 1 their plans are
+spread over that many CUDA streams (largest classes first, each to the
+least-loaded stream), forked from and joined back into the runner's stream,
+so the graph holds parallel branches and one class's kernels fill the SMs
+another leaves idle (grid tails, small reduce / scan / finalize launches).  The autotuner picks, per class, the paint variant (tile sort or
 direct atomics) and the tile edge by timing every candidate on the class's own
 catalogs; results do not depend on the choice (both variants paint the same
 int64 fixed-point cells up to one rounding of each deposit).
@@ -98,6 +102,18 @@ def tune_key(key: tuple, mean_objects: float) -> str:
                                            int(round(math.log2(max(mean_objects, 1.0)))))
 
 
+def assign_streams(loads, nstreams: int) -> list:
+    """Stream index of each class: largest load first, each to the stream
+    with the least load so far (ties: the lower index)."""
+    where = [0] * len(loads)
+    total = [0] * max(int(nstreams), 1)
+    for k in sorted(range(len(loads)), key=lambda k: (-loads[k], k)):
+        s = min(range(len(total)), key=lambda j: (total[j], j))
+        where[k] = s
+        total[s] += loads[k]
+    return where
+
+
 class Autotuner:
     """Times each (paint variant, tile edge) candidate on a sample of a class's
     catalogs and keeps the fastest per tune_key.  The cache can be saved to and
@@ -169,6 +185,7 @@ class _Class:
     pos: object
     weights: object
     choice: tuple
+    stream_index: int = 0
     plan: object = None
     results: list = field(default_factory=list)
 
@@ -184,13 +201,16 @@ class BatchPower:
 
     def __init__(self, catalogs, box_size, dk=None, kmin=0.0, kmax=None, nmu=0, poles=(0, 2, 4),
                  precision="f32", compensated=True, subtract_shot=True, tuner: Autotuner | None = None,
-                 graph: bool = True, stream=None):
+                 graph: bool = True, stream=None, streams: int = 1):
         import torch
         if not catalogs:
             raise ValueError("no catalogs")
+        if streams < 1:
+            raise ValueError("streams must be at least 1")
         self.torch = torch
         self.n = len(catalogs)
         self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.streams = [self.stream] + [torch.cuda.Stream() for _ in range(streams - 1)]
         self.cfg_kwargs = dict(box_size=box_size, dk=dk, kmin=kmin, kmax=kmax, nmu=nmu, poles=poles,
                                precision=precision, compensated=compensated,
                                subtract_shot=subtract_shot)
@@ -199,7 +219,10 @@ class BatchPower:
         self.launches_per_run = 0
         self.stream.wait_stream(torch.cuda.current_stream())     # catalogs written on it
         try:
-            for key, idx in group_classes(catalogs, precision).items():
+            groups = group_classes(catalogs, precision)
+            where = assign_streams([sum(catalogs[i].n for i in idx) for idx in groups.values()],
+                                   len(self.streams))
+            for (key, idx), si in zip(groups.items(), where):
                 sizes = [catalogs[i].n for i in idx]
                 offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
                 with torch.cuda.stream(self.stream):
@@ -211,8 +234,8 @@ class BatchPower:
                 cfg = make_config(nmesh=key[0], window=key[1], interlaced=key[2], batch=len(idx),
                                   tile=choice[1], paint_variant=choice[0],
                                   capacity=max(int(offsets[-1]), 1), **self.cfg_kwargs)
-                c = _Class(key, idx, offsets, pos, w, choice)
-                c.plan = pk_plan(cfg, self.stream)
+                c = _Class(key, idx, offsets, pos, w, choice, si)
+                c.plan = pk_plan(cfg, self.streams[si])
                 self.classes.append(c)
             self.stream.synchronize()
             if graph:
@@ -222,9 +245,19 @@ class BatchPower:
             raise
 
     def _enqueue(self):
+        torch = self.torch
+        if len(self.streams) > 1:                 # fork: every class stream after the runner's
+            fork = torch.cuda.Event()
+            fork.record(self.stream)
+            for s in self.streams[1:]:
+                s.wait_event(fork)
         for c in self.classes:
             pk_paint_many(c.plan, c.pos, c.offsets, c.weights)
             pk_compute(c.plan)
+        for s in self.streams[1:]:                # join: the runner's stream after every class
+            e = torch.cuda.Event()
+            e.record(s)
+            self.stream.wait_event(e)
 
     def _capture(self):
         torch = self.torch

@@ -66,3 +66,15 @@ def test_mock_set_specs_are_seeded_and_follow_their_distributions():
     assert {s["nmesh"] for s in a} == {128, 192, 256}
     assert {s["window"] for s in a} == {"cic", "tsc"}
     assert len({s["seed"] for s in a}) == 256
+
+
+def test_assign_streams_balances_largest_first():
+    from paper_1712_05834_gb300.batch import assign_streams
+    assert assign_streams([5, 1, 9, 3], 1) == [0, 0, 0, 0]
+    # 9 -> s0, 5 -> s1, 3 -> s1 (5 < 9), 1 -> s1 (8 < 9)
+    assert assign_streams([5, 1, 9, 3], 2) == [1, 1, 0, 1]
+    assert assign_streams([4, 4, 4], 3) == [0, 1, 2]
+    assert assign_streams([], 2) == []
+    w = assign_streams([7, 7, 2, 2, 2, 2, 2], 2)
+    loads = [sum(x for x, s in zip([7, 7, 2, 2, 2, 2, 2], w) if s == k) for k in range(2)]
+    assert sorted(loads) == [11, 13]          # greedy, not optimal: 7, 2, 2, 2 / 7, 2, 2

@@ -124,8 +124,8 @@ def test_capture_refuses_growth_and_host_inputs(pk):
         pk.pk_destroy(plan)
 
 
-@pytest.mark.parametrize("graph", [True, False])
-def test_size_class_batches_match_one_at_a_time(pk, graph):
+@pytest.mark.parametrize("graph,streams", [(True, 1), (False, 1), (True, 3), (False, 2)])
+def test_size_class_batches_match_one_at_a_time(pk, graph, streams):
     import torch
     import synth
     from paper_1712_05834_gb300 import batch
@@ -134,8 +134,9 @@ def test_size_class_batches_match_one_at_a_time(pk, graph):
     specs = synth.mock_set_specs(14, synth.seed_for(4, 500), n_lo=2e3, n_hi=6e4, meshes=(32, 48, 64))
     cats = _mocks(torch, specs, L)
     tuner = batch.Autotuner(sample=4, repeats=1)
-    with batch.BatchPower(cats, L, dk=dk, tuner=tuner, graph=graph) as bp:
+    with batch.BatchPower(cats, L, dk=dk, tuner=tuner, graph=graph, streams=streams) as bp:
         assert len(bp.classes) == len(batch.group_classes(cats))
+        assert len({c.stream_index for c in bp.classes}) == min(streams, len(bp.classes))
         res = bp.run()
         res2 = bp.run()
         assert bp.launches_per_run >= 5 * len(bp.classes)
