@@ -68,7 +68,7 @@ void free_plan(pk_plan_s *p) {
     cudaStreamSynchronize(p->st);
     for (cufftHandle h : p->fft) cufftDestroy(h);
     void *dev[] = {p->mesh, p->d_count, p->d_off, p->d_scan_tmp, p->d_sorted,
-                   p->d_stage, p->d_item_off, p->d_wsums, p->d_wmax, p->d_cw, p->d_ph,
+                   p->d_stage, p->d_item_off, p->d_wsums, p->d_wpart, p->d_wmax, p->d_cw, p->d_ph,
                    p->d_kedge, p->d_partial, p->d_sums2, p->d_res, p->d_modes1d, p->d_modes2d,
                    p->d_err, p->d_acc, p->fft_work, p->d_xres, p->d_proj, p->d_tw};
     for (void *d : dev)
@@ -375,6 +375,7 @@ static pk_status plan_build(pk_plan_s *P, const pk_config *cfg) {
     PK_CUDA(P, dev_alloc(&P->d_scan_tmp, sizeof(uint32_t) * scan_tmp_elems(keys_all)));
     PK_CUDA(P, dev_alloc(&P->d_item_off, sizeof(int64_t) * (P->B + 1)));
     PK_CUDA(P, dev_alloc(&P->d_wsums, sizeof(double) * 4 * P->B));
+    PK_CUDA(P, dev_alloc(&P->d_wpart, sizeof(double) * wsum_partial_elems(P->B)));
     PK_CUDA(P, dev_alloc(&P->d_wmax, sizeof(unsigned) * P->B));
     PK_CUDA(P, dev_alloc(&P->d_err, sizeof(int)));
     PK_CUDA(P, cudaMemset(P->d_err, 0, sizeof(int)));
@@ -536,7 +537,8 @@ static pk_status paint_atomic(pk_plan_s *P, const void *dpos, int dtype, const f
     }
     if (tm) PK_CUDA(P, cudaEventRecord(P->tev[1], st));   // no sort stage
     PK_CUDA(P, launch_paint_atomic(dpos, dtype, dw, dv, P->d_item_off, nitems, max_n, P->pg, P->p, P->nm, P->S,
-                                   P->d_acc, P->d_wsums, P->d_wmax, st));
+                                   P->d_acc, P->d_wsums, P->d_wpart, P->d_wmax, st));
+    if (dw != nullptr || dv != nullptr || dtype == PK_F32X4) launches += 1;   // the weight sums' reduce
     PK_CUDA(P, launch_acc_to_mesh(P->d_acc, nitems, P->nm, P->N, P->S, P->f64, P->mesh,
                                   P->nm * P->mesh_reals, P->mesh_reals, accumulate, P->nsm, st));
     if (tm) PK_CUDA(P, cudaEventRecord(P->tev[2], st));
@@ -637,7 +639,8 @@ static pk_status paint_impl(pk_plan_s *P, const void *pos, int dtype, const floa
         PK_CUDA(P, cudaMemsetAsync(P->d_wmax, 0, sizeof(unsigned) * nitems, st));
     }
     PK_CUDA(P, launch_sort_count(dpos, dtype, dw, dv, P->d_item_off, nitems, max_n, P->pg, P->d_count,
-                                 P->d_wsums, P->d_wmax, st));
+                                 P->d_wsums, P->d_wpart, P->d_wmax, st));
+    if (dw != nullptr || dv != nullptr || dtype == PK_F32X4) launches += 1;   // the weight sums' reduce
     PK_CUDA(P, launch_scan(P->d_count, nkeys, P->d_off, P->d_scan_tmp, &launches, st));
     PK_CUDA(P, launch_sort_scatter(dpos, dtype, dw, dv, P->d_item_off, nitems, max_n, P->pg, P->d_off,
                                    P->d_count, P->d_sorted, P->d_err, st));

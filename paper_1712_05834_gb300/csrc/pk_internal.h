@@ -66,7 +66,9 @@ cudaError_t launch_upload_i64(int64_t *dst, const int64_t *src, int n, int *laun
 // each object deposits W V and the sums keep sum W, sum (W V)^2, sum |W V|.
 cudaError_t launch_sort_count(const void *pos, int dtype, const float *w, const float *vals,
                               const int64_t *item_off, int nitems, int64_t max_n, const PaintGeom &g,
-                              uint32_t *count, double *wsums, unsigned *wmax, cudaStream_t st);
+                              uint32_t *count, double *wsums, double *wpart, unsigned *wmax, cudaStream_t st);
+// Doubles of the per-block weight-sum rows (wpart) for nitems catalogs.
+size_t wsum_partial_elems(int nitems);
 cudaError_t launch_scan(const uint32_t *in, int64_t n, uint32_t *out, uint32_t *tmp, int *launches,
                         cudaStream_t st);
 cudaError_t launch_scan64(const unsigned long long *in, int64_t n, unsigned long long *out,
@@ -86,7 +88,7 @@ cudaError_t launch_paint_tiles(const float4 *sorted, const uint32_t *off, int ni
 cudaError_t launch_paint_atomic(const void *pos, int dtype, const float *w, const float *vals,
                                 const int64_t *item_off, int nitems, int64_t max_n, const PaintGeom &g,
                                 int window, int nmesh, int S, unsigned long long *acc, double *wsums,
-                                unsigned *wmax, cudaStream_t st);
+                                double *wpart, unsigned *wmax, cudaStream_t st);
 cudaError_t launch_acc_to_mesh(unsigned long long *acc, int nitems, int nmesh, int N, int S, int f64,
                                void *mesh, long long item_stride, long long mesh_stride, int accumulate,
                                int nsm, cudaStream_t st);

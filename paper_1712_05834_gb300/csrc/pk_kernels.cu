@@ -7,6 +7,8 @@
 //                   face, interior, near the high face -- 27 classes) and
 //                   count objects per (tile, class) key (reductions whose
 //                   result nobody waits for); sum w, w^2, |w| and max |w|.
+//   k_wsum_reduce   weighted catalogs: the paint blocks' rows of weight sums
+//                   added in a fixed order (run-to-run identical sums).
 //   k_scan_*        exclusive scan of the key counts (uint32).
 //   k_sort_scatter  write one float4 (home-tile-local x, y, z, w) per object
 //                   at offset[key] + (its key's count, decremented): the
@@ -59,6 +61,7 @@ namespace pk {
 namespace {
 
 constexpr int kCountThreads = 256;
+constexpr unsigned kWsumBlocks = 2048;  // blocks per catalog of the passes that sum the weights
 constexpr int kPaintThreads = 256;
 constexpr int kBinThreads = 256;
 constexpr int kBinVec = 4;            // consecutive modes per thread
@@ -181,12 +184,15 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
-// Block reduction of the weight sums: wsums[4 * item + {0,1,2}] = sum W,
-// sum (W V)^2, sum |W V|; wmax[item] = max |W V| (float bits), with W the
-// weight and W V the painted amplitude.
+// Block reduction of the weight sums: sum W, sum (W V)^2, sum |W V| of the
+// block's objects into its row wpart[(item * gridDim.x + block) * 3 + k]
+// (summed over the blocks in a fixed order by k_wsum_reduce, so the sums do
+// not depend on which block finishes first); wmax[item] = max |W V| (float
+// bits, order-free), with W the weight and W V the painted amplitude.
+// Unweighted: wsums[4 * item + {0,1,2}] += n, wmax = 1.
 __device__ __forceinline__ void flush_wsums(double sw, double sw2, double swa, float mw, bool weighted,
                                             int item, int64_t n_item, double *__restrict__ wsums,
-                                            unsigned *__restrict__ wmax) {
+                                            double *__restrict__ wpart, unsigned *__restrict__ wmax) {
     if (weighted) {
         __shared__ double red[3][kCountThreads / 32];
         __shared__ float redm[kCountThreads / 32];
@@ -205,7 +211,7 @@ __device__ __forceinline__ void flush_wsums(double sw, double sw2, double swa, f
         if (threadIdx.x < 3) {
             double t = 0.0;
             for (int k = 0; k < kCountThreads / 32; ++k) t += red[threadIdx.x][k];
-            if (t != 0.0) atomicAdd(wsums + 4 * item + threadIdx.x, t);
+            wpart[((size_t)item * gridDim.x + blockIdx.x) * 3 + threadIdx.x] = t;
         } else if (threadIdx.x == 3) {
             float m = 0.0f;
             for (int k = 0; k < kCountThreads / 32; ++k) m = fmaxf(m, redm[k]);
@@ -215,6 +221,29 @@ __device__ __forceinline__ void flush_wsums(double sw, double sw2, double swa, f
         atomicAdd(wsums + 4 * item + threadIdx.x, (double)n_item);   // exact below 2^53
         if (threadIdx.x == 0) atomicMax(wmax + item, __float_as_uint(1.0f));
     }
+}
+
+// Fixed-order sum of the blocks' weight-sum rows of catalog blockIdx.x:
+// thread t adds rows t, t + 256, ... in turn, then a fixed tree; the result
+// is added to wsums[4 * item + k] (one writer per value).
+__global__ void __launch_bounds__(256)
+k_wsum_reduce(const double *__restrict__ wpart, int nblk, double *__restrict__ wsums) {
+    __shared__ double red[3][256];
+    const int item = blockIdx.x, t = threadIdx.x;
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int b = t; b < nblk; b += 256)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a[k] += wpart[((size_t)item * nblk + b) * 3 + k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) red[k][t] = a[k];
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (t < h)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) red[k][t] += red[k][t + h];
+        __syncthreads();
+    }
+    if (t < 3) wsums[4 * item + t] += red[t][0];
 }
 
 // Key of an object: (catalog, home tile, boundary class).
@@ -230,7 +259,7 @@ template <int DT, bool WEIGHTED>
 __global__ void __launch_bounds__(kCountThreads)
 k_sort_count(const void *__restrict__ pos, const float *__restrict__ w, const float *__restrict__ vals,
              const int64_t *__restrict__ item_off, PaintGeom g, uint32_t *__restrict__ count,
-             double *__restrict__ wsums, unsigned *__restrict__ wmax) {
+             double *__restrict__ wsums, double *__restrict__ wpart, unsigned *__restrict__ wmax) {
     using R = typename PosReal<DT>::type;
     const int item = blockIdx.y;
     const int64_t beg = item_off[item], end = item_off[item + 1];
@@ -250,7 +279,7 @@ k_sort_count(const void *__restrict__ pos, const float *__restrict__ w, const fl
             mw = fmaxf(mw, fabsf(o.a));
         }
     }
-    flush_wsums(sw, sw2, swa, mw, WEIGHTED, item, end - beg, wsums, wmax);
+    flush_wsums(sw, sw2, swa, mw, WEIGHTED, item, end - beg, wsums, wpart, wmax);
 }
 
 // Tile sort, pass 2: each object takes the last free slot of its key's range
@@ -979,7 +1008,7 @@ __global__ void __launch_bounds__(kCountThreads)
 k_paint_atomic(const void *__restrict__ pos, const float *__restrict__ w, const float *__restrict__ vals,
                const int64_t *__restrict__ item_off, PaintGeom g, int S, bool weighted,
                unsigned long long *__restrict__ acc, double *__restrict__ wsums,
-               unsigned *__restrict__ wmax) {
+               double *__restrict__ wpart, unsigned *__restrict__ wmax) {
     using R = typename PosReal<DT>::type;
     const int item = blockIdx.y;
     const int64_t beg = item_off[item], end = item_off[item + 1];
@@ -1009,7 +1038,7 @@ k_paint_atomic(const void *__restrict__ pos, const float *__restrict__ w, const 
             mw = fmaxf(mw, fabsf(o.a));
         }
     }
-    flush_wsums(sw, sw2, swa, mw, weighted, item, end - beg, wsums, wmax);
+    flush_wsums(sw, sw2, swa, mw, weighted, item, end - beg, wsums, wpart, wmax);
 }
 
 template <typename M>
@@ -1465,20 +1494,27 @@ int paint_classes() { return kClasses; }
 
 cudaError_t launch_sort_count(const void *pos, int dtype, const float *w, const float *vals,
                               const int64_t *item_off, int nitems, int64_t max_n, const PaintGeom &g,
-                              uint32_t *count, double *wsums, unsigned *wmax, cudaStream_t st) {
-    dim3 grid(grid_for(max_n, kCountThreads, 1u << 20), nitems);
+                              uint32_t *count, double *wsums, double *wpart, unsigned *wmax, cudaStream_t st) {
     const bool weighted = w != nullptr || vals != nullptr || dtype == PK_F32X4;
+    dim3 grid(grid_for(max_n, kCountThreads, weighted ? kWsumBlocks : 1u << 20), nitems);
 #define PK_COUNT(DT)                                                                                    \
-    if (weighted) k_sort_count<DT, true><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, count, wsums, wmax); \
-    else k_sort_count<DT, false><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, count, wsums, wmax);
+    if (weighted) k_sort_count<DT, true><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, count, wsums, wpart, wmax); \
+    else k_sort_count<DT, false><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, count, wsums, wpart, wmax);
     switch (dtype) {
     case PK_F32: PK_COUNT(PK_F32) break;
     case PK_F64: PK_COUNT(PK_F64) break;
     default: PK_COUNT(PK_F32X4) break;
     }
 #undef PK_COUNT
+    if (weighted) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_wsum_reduce<<<nitems, 256, 0, st>>>(wpart, (int)grid.x, wsums);
+    }
     return cudaGetLastError();
 }
+
+size_t wsum_partial_elems(int nitems) { return (size_t)nitems * kWsumBlocks * 3; }
 
 cudaError_t launch_sort_scatter(const void *pos, int dtype, const float *w, const float *vals,
                                 const int64_t *item_off, int nitems, int64_t max_n, const PaintGeom &g,
@@ -1607,24 +1643,30 @@ cudaError_t launch_paint_tiles(const float4 *sorted, const uint32_t *off, int ni
 template <int DT, int P, int NM>
 static cudaError_t atomic_inst(const void *pos, const float *w, const float *vals, const int64_t *item_off, int nitems,
                                int64_t max_n, const PaintGeom &g, int S, bool weighted,
-                               unsigned long long *acc, double *wsums, unsigned *wmax, cudaStream_t st) {
-    dim3 grid(grid_for(max_n, kCountThreads, 1u << 20), nitems);
+                               unsigned long long *acc, double *wsums, double *wpart, unsigned *wmax,
+                               cudaStream_t st) {
+    dim3 grid(grid_for(max_n, kCountThreads, weighted ? kWsumBlocks : 1u << 20), nitems);
     k_paint_atomic<DT, P, NM><<<grid, kCountThreads, 0, st>>>(pos, w, vals, item_off, g, S, weighted, acc,
-                                                             wsums, wmax);
+                                                             wsums, wpart, wmax);
+    if (weighted) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_wsum_reduce<<<nitems, 256, 0, st>>>(wpart, (int)grid.x, wsums);
+    }
     return cudaGetLastError();
 }
 
 template <int DT>
 static cudaError_t atomic_dispatch(const void *pos, const float *w, const float *vals, const int64_t *item_off, int nitems,
                                    int64_t max_n, const PaintGeom &g, int window, int nmesh, int S,
-                                   bool weighted, unsigned long long *acc, double *wsums, unsigned *wmax,
-                                   cudaStream_t st) {
+                                   bool weighted, unsigned long long *acc, double *wsums, double *wpart,
+                                   unsigned *wmax, cudaStream_t st) {
 #define PK_ATOMIC_CASE(P)                                                                              \
     if (window == P)                                                                                   \
         return nmesh == 2 ? atomic_inst<DT, P, 2>(pos, w, vals, item_off, nitems, max_n, g, S, weighted, acc, \
-                                                  wsums, wmax, st)                                    \
+                                                  wsums, wpart, wmax, st)                             \
                           : atomic_inst<DT, P, 1>(pos, w, vals, item_off, nitems, max_n, g, S, weighted, acc, \
-                                                  wsums, wmax, st);
+                                                  wsums, wpart, wmax, st);
     PK_ATOMIC_CASE(2)
     PK_ATOMIC_CASE(3)
     PK_ATOMIC_CASE(4)
@@ -1635,18 +1677,18 @@ static cudaError_t atomic_dispatch(const void *pos, const float *w, const float 
 cudaError_t launch_paint_atomic(const void *pos, int dtype, const float *w, const float *vals,
                                 const int64_t *item_off, int nitems, int64_t max_n, const PaintGeom &g,
                                 int window, int nmesh, int S, unsigned long long *acc, double *wsums,
-                                unsigned *wmax, cudaStream_t st) {
+                                double *wpart, unsigned *wmax, cudaStream_t st) {
     const bool weighted = w != nullptr || vals != nullptr || dtype == PK_F32X4;
     switch (dtype) {
     case PK_F32:
         return atomic_dispatch<PK_F32>(pos, w, vals, item_off, nitems, max_n, g, window, nmesh, S, weighted, acc,
-                                       wsums, wmax, st);
+                                       wsums, wpart, wmax, st);
     case PK_F64:
         return atomic_dispatch<PK_F64>(pos, w, vals, item_off, nitems, max_n, g, window, nmesh, S, weighted, acc,
-                                       wsums, wmax, st);
+                                       wsums, wpart, wmax, st);
     default:
         return atomic_dispatch<PK_F32X4>(pos, w, vals, item_off, nitems, max_n, g, window, nmesh, S, weighted,
-                                         acc, wsums, wmax, st);
+                                         acc, wsums, wpart, wmax, st);
     }
 }
 

@@ -48,6 +48,7 @@ struct pk_plan_s {
     size_t stage_cap = 0;
     int64_t *d_item_off = nullptr;   // catalog offsets of the last paint call
     double *d_wsums = nullptr;       // per catalog: sum w, sum w^2, sum |w|, spare
+    double *d_wpart = nullptr;       // per catalog and paint block: its three weight sums
     unsigned *d_wmax = nullptr;      // per catalog: max |w| as float bits
     int *d_err = nullptr;           // bit 1: tile sort inconsistency (never expected)
     unsigned long long *d_acc = nullptr;   // atomic variant: B * nm * N^3 int64 cells
