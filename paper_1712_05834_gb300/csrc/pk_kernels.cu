@@ -517,31 +517,44 @@ __device__ __forceinline__ void deposit_flat(unsigned *sm, int cell0, unsigned t
     }
 }
 
-// ---- one-sweep paint of 16^3 tiles into a padded layout (unit weights, PCS) ----
+// ---- one-sweep paint of 16^3 tiles into a padded layout (unit weights, TSC and PCS) ----
 // Shared layout: cell (x, y, z) of the tile's mesh m at word
 //   m * kWords + x * kXS + y * kYS + kZlo + z,
 // where every row of z holds a halo [-kZlo, kYS - kZlo) wide enough for every
-// deposit of every candidate of the tile (objects of the tile and the
-// boundary classes of its neighbours, both meshes), so a deposit needs no
-// bounds test along z; a row outside the tile along x or y is skipped by a
-// predicate (a word shared by many lanes of one atomic instruction would
-// serialize them).  Each deposit is then one FFMA, one IADD and one 32-bit
-// shared atomic at an immediate offset from its row.
+// deposit of every window that reaches the tile along z (objects of the tile
+// and the boundary classes of its neighbours, both meshes), so a deposit
+// needs no bounds test along z; a window wholly outside the tile along z (the
+// other mesh of a boundary candidate) and a row outside the tile along x or
+// y are skipped by predicates (a word shared by many lanes of one atomic
+// instruction would serialize them).  Each deposit is then one FFMA, one
+// IADD and one 32-bit shared atomic at an immediate offset from its row.
+//
+// The strides are odd: candidates arrive grouped by (tile, boundary class),
+// and on a lattice-like catalog a warp's lanes share z offsets, so with even
+// strides (plane 384 = 0 mod 32 words, rows 24) their deposits fell on a few
+// banks (5.1 shared wavefronts per atomic instruction measured on a
+// Zel'dovich lattice at 0.125 objects per cell); rows of 25 and planes of 401
+// words spread them over all 32 banks (PCS + interlacing 1.93 -> 1.22 ms on
+// that lattice at 512^3, 1.01 -> 0.92 ms on the log-normal catalog; TSC
+// with rows of 21 and planes of 337: 1.02 -> 0.69 and 0.537 -> 0.526 ms).
 template <int P>
 struct SweepLayout {
     static constexpr int T = 16;
-    static constexpr int Zlo = P == 2 ? 2 : 4;        // z halo below the tile
-    static constexpr int YS = P == 2 ? 20 : 24;       // row stride (even: paired flush loads)
-    static constexpr int XS = T * YS;                 // plane stride
+    static constexpr int Zlo = P == 4 ? 4 : P - 1;    // z halo below the tile
+    static constexpr int YS = P == 4 ? 25 : (P == 3 ? 21 : 19);   // row stride
+    static constexpr int XS = P == 4 ? 401 : (P == 3 ? 337 : 305);  // plane stride
     static constexpr int Words = T * XS;              // one mesh (a multiple of 4 words)
+    // first nodes of the windows that reach the tile along z: any other
+    // window lies wholly outside it and deposits nothing
     static constexpr int BzMin = -Zlo, BzMax = YS - Zlo - P;
+    static_assert(Zlo >= P - 1 && BzMax >= T - 1, "the halo must hold every window that reaches the tile");
+    static_assert(XS >= T * YS && Words % 4 == 0, "rows inside their plane; 16-byte zeroing");
 };
 
 // Deposits of one candidate (tile-frame coordinates x, y, z in cells, weight
 // ws already scaled by 2^S) into the mesh whose first word is sm.  A first
 // node bz outside [BzMin, BzMax] only occurs for a window lying wholly
-// outside the tile along z (its cells stay in the halo either way), so the
-// clamp changes no flushed cell and keeps every access in its row.
+// outside the tile along z: it deposits nothing.
 template <int P, bool SKIP_PLANES>
 __device__ __forceinline__ void sweep_deposit(unsigned *sm, float x, float y, float z, float ws) {
     using Lay = SweepLayout<P>;
@@ -551,7 +564,8 @@ __device__ __forceinline__ void sweep_deposit(unsigned *sm, float x, float y, fl
     spline_weights<P>(x, bx, wx);
     spline_weights<P>(y, by, wy);
     spline_weights<P>(z, bz, wz);
-    bz = min(max(bz, Lay::BzMin), Lay::BzMax) + Lay::Zlo;
+    if (bz < Lay::BzMin || bz > Lay::BzMax) return;
+    bz += Lay::Zlo;
     int ox[P], oy[P];
 #pragma unroll
     for (int a = 0; a < P; ++a) {
@@ -577,7 +591,8 @@ __device__ __forceinline__ void sweep_deposit(unsigned *sm, float x, float y, fl
 }
 
 // Write mesh words of the padded layout (cells of the tile only) to the r2c
-// mesh: two cells per thread and store, as flush_tile.
+// mesh: two cells per thread and store, as flush_tile (two 32-bit loads: the
+// odd strides leave a pair of cells 4-byte aligned only).
 template <typename M, int P>
 __device__ __forceinline__ void sweep_flush(const unsigned *sm, float inv_scale, M *__restrict__ dst0, int N,
                                             long long pitch, int accumulate) {
@@ -595,7 +610,7 @@ __device__ __forceinline__ void sweep_flush(const unsigned *sm, float inv_scale,
     const long long gstep = (long long)planes * N * pitch;
 #pragma unroll 2
     for (int k = 0; k < T / planes; ++k, w += planes * Lay::XS, dst += gstep) {
-        const uint2 l2 = *reinterpret_cast<const uint2 *>(sm + w);
+        const uint2 l2 = make_uint2(sm[w], sm[w + 1]);
         M2 v;
         v.x = (M)l2.x * (M)inv_scale;
         v.y = (M)l2.y * (M)inv_scale;
@@ -880,10 +895,10 @@ k_paint_tiles(const float4 *__restrict__ sorted, const uint32_t *__restrict__ of
     // copy (nothing to stage), with branch-free deposits; an interlaced pair
     // goes into lo (mesh 0) and hi (mesh 1) together.
     const bool sweep = sp.fast == 2;
-    // PCS sweeps of 16^3 tiles deposit into the padded layout (SweepLayout):
-    // measured 1.02 against 1.20 ms for PCS + interlacing at Nmesh 512, while
-    // CIC and TSC keep the compact layout (0.55 against 0.61 ms for TSC)
-    const bool kPadded = sweep && TC == 16 && P == 4;
+    // TSC and PCS sweeps of 16^3 tiles deposit into the padded layout
+    // (SweepLayout); CIC keeps the compact one (its padded layout with even
+    // strides measured 0.69 against 0.54 ms)
+    const bool kPadded = sweep && TC == 16 && (P == 4 || P == 3);
     const bool staged_once = total <= (uint32_t)kStage;
     if (staged_once && !sweep) stage_candidates(sorted, s_beg, s_pre, T, 0u, total, scale, cand);
     const long long pitch = 2LL * (g.N / 2 + 1);
@@ -1593,7 +1608,9 @@ cudaError_t launch_scan64(const unsigned long long *in, int64_t n, unsigned long
 
 size_t paint_smem_bytes(int T, int window) {
     const size_t general = (size_t)2 * T * T * T * sizeof(unsigned) + (size_t)kStage * sizeof(float4);
-    const size_t padded = (T == 16 && window == 4) ? (size_t)2 * SweepLayout<4>::Words * sizeof(unsigned) : 0;
+    const size_t padded = T != 16 ? 0
+                          : window == 4 ? (size_t)2 * SweepLayout<4>::Words * sizeof(unsigned)
+                          : window == 3 ? (size_t)2 * SweepLayout<3>::Words * sizeof(unsigned) : 0;
     return general > padded ? general : padded;
 }
 
