@@ -57,7 +57,8 @@ ResultLayout result_layout(int nk, int nmu);
 
 // ---- launchers (pk_kernels.cu); all asynchronous on `st` ----
 int paint_classes();                  // boundary classes per tile (27)
-size_t paint_smem_bytes(int T, int window);   // dynamic shared memory of one tile-paint CTA
+// dynamic shared memory of one tile-paint CTA painting nmesh meshes
+size_t paint_smem_bytes(int T, int window, int nmesh = 2);
 size_t scan_tmp_elems(int64_t n);
 // dst[0 .. n) = src[0 .. n) for a host array src, through kernel parameters
 // (the host array may be reused as soon as the call returns).

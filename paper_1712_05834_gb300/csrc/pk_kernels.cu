@@ -1606,11 +1606,11 @@ cudaError_t launch_scan64(const unsigned long long *in, int64_t n, unsigned long
     return scan_impl<unsigned long long>(in, n, out, tmp, launches, st);
 }
 
-size_t paint_smem_bytes(int T, int window) {
+size_t paint_smem_bytes(int T, int window, int nmesh) {
     const size_t general = (size_t)2 * T * T * T * sizeof(unsigned) + (size_t)kStage * sizeof(float4);
     const size_t padded = T != 16 ? 0
-                          : window == 4 ? (size_t)2 * SweepLayout<4>::Words * sizeof(unsigned)
-                          : window == 3 ? (size_t)2 * SweepLayout<3>::Words * sizeof(unsigned) : 0;
+                          : window == 4 ? (size_t)nmesh * SweepLayout<4>::Words * sizeof(unsigned)
+                          : window == 3 ? (size_t)nmesh * SweepLayout<3>::Words * sizeof(unsigned) : 0;
     return general > padded ? general : padded;
 }
 
@@ -1619,7 +1619,7 @@ static cudaError_t paint_inst(const float4 *sorted, const uint32_t *off, int nit
                               const PaintGeom &g, int S, const unsigned *wmax, float wmax_deposit,
                               void *mesh, long long item_stride, long long mesh_stride, int accumulate,
                               cudaStream_t st) {
-    const size_t smem = paint_smem_bytes(g.T, P);
+    const size_t smem = paint_smem_bytes(g.T, P, NM);   // one padded mesh fits the general area
     const long long nblocks = (long long)nitems * g.ntiles;
     if (nblocks <= 0) return cudaSuccess;
     if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
