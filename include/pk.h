@@ -67,9 +67,15 @@ typedef enum {
 } pk_dtype;
 
 /* Mesh / transform precision.  Both paint into int64 fixed point (so the
- * mesh is bit-identical run to run) and sum bins in FP64. */
+ * mesh is bit-identical run to run) and form the catalog weight sums in FP64
+ * in a fixed order (also bit-identical run to run).
+ * PK_MESH_F32: the library's own r2c transform at nmesh 128, 192, 256, 512
+ * and 2048 (cuFFT R2C otherwise; see pk_use_own_fft); bins summed per CTA in
+ * FP32 with shared-memory atomics, whose order (and so the last bits of
+ * P(k)) can vary between runs, then across CTAs in FP64.
+ * PK_MESH_F64: cuFFT D2Z; bins summed in FP64. */
 typedef enum {
-    PK_MESH_F32 = 0,   /* FP32 mesh, cuFFT R2C, FP32 per-mode arithmetic        */
+    PK_MESH_F32 = 0,   /* FP32 mesh, FP32 per-mode arithmetic                   */
     PK_MESH_F64 = 1    /* FP64 mesh, cuFFT D2Z, FP64 per-mode arithmetic        */
 } pk_precision;
 
@@ -104,8 +110,9 @@ typedef struct {
     int tile;               /* paint tile edge in cells; 0 -> automatic          */
     int paint_variant;      /* pk_paint_variant                                  */
     int64_t capacity;       /* objects per paint call to reserve at plan time so
-                               that pk_paint never allocates or waits; 0 -> the
-                               first paint reserves what it needs                */
+                               that pk_paint never allocates or waits (16 bytes
+                               of device memory per object for the tile sort);
+                               0 -> the first paint reserves what it needs       */
 } pk_config;
 
 /* Result of one catalog.  All pointers are host memory owned by the plan and
